@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the homogenized-MGPCG topology-optimisation hot path on GB300.
+
+One step = one pass of the whole hot path over the synthetic workload:
+set_density (homogenized levels + coarsest factorisation), state solve from
+u = 0 (mixed precision: FP32 inner MGPCG inside FP64 refinement), compliance +
+sensitivity, filter transpose + OC update.  The metric is the state-solve time
+in seconds (lower is better); the compliance of the mixed solve is checked
+against an all-FP64 GPU solve of the same grid to 1e-10.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--dims NXxNYxNZ] [--fp64-ref full|skip]
+                  [--cpu-baseline on|off]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(the solve needs no data from other ranks); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "cantilever_768x384x384_mixed"
+CPU_SAMPLE_DIMS = (96, 48, 48)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--dims", default=None, help="override grid, e.g. 96x48x48")
+    ap.add_argument("--levels", type=int, default=None)
+    ap.add_argument("--rel-tol", type=float, default=1e-8,
+                    help="relative residual of the timed (mixed) solve")
+    ap.add_argument("--fp64-tol", type=float, default=1e-6,
+                    help="relative residual of the timed all-FP64 comparison solve")
+    ap.add_argument("--fp64-ref", choices=["full", "skip"], default="full")
+    ap.add_argument("--cpu-baseline", choices=["on", "off"], default="on")
+    ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def workload(args):
+    import synth
+    w = dict(synth.WORKLOADS[args.workload])
+    dims = tuple(int(v) for v in args.dims.split("x")) if args.dims else tuple(w["dims"])
+    levels = args.levels or w["levels"]
+    while levels > 1 and any(d % (1 << (levels - 1)) for d in dims):
+        levels -= 1
+    return w, dims, levels
+
+
+def physical_density(grid, name, dims, dev):
+    """The workload's density recipe on the device (filtering with the
+    library's own filter kernel)."""
+    import torch
+    import synth
+    d = synth.WORKLOADS[name]["density"]
+    raw = torch.tensor(synth.raw_density(name, dims), device=dev)
+    if d["kind"] == "const":
+        return raw
+    rho = grid.filter(d["rmin"], raw)
+    if "clip" in d:
+        rho.clamp_(d["clip"][0], d["clip"][1])
+    return rho
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, single-threaded, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_sample(name, dims, rel_tol):
+    """Oracle state solve of the workload recipe at `dims`; returns seconds."""
+    import numpy as np
+    import synth
+    from oracle import filter as oflt, state as ostate
+    w = synth.WORKLOADS[name]
+    pb = synth.make_problem(name, dims)
+    raw = synth.raw_density(name, dims)
+    d = w["density"]
+    rho = raw if d["kind"] == "const" else oflt.density_filter(raw, dims, d["rmin"])
+    if "clip" in d:
+        rho = np.clip(rho, *d["clip"])
+    t0 = time.perf_counter()
+    u, info = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=rel_tol, method="mgpcg", return_info=True)
+    return time.perf_counter() - t0, info
+
+
+def run_cpu_child(args):
+    _, _, _ = None, None, None
+    w, dims, _ = workload(args)
+    sample = CPU_SAMPLE_DIMS
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, info = cpu_sample(args.workload, sample, args.rel_tol)
+        if i >= args.warmup:
+            times.append(t)
+    print(json.dumps({"times": times, "sample_dims": sample, "iters": info["iters"]}))
+
+
+def cpu_baseline(args, steps=1, warmup=0):
+    """Spawns the oracle in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "--workload", args.workload,
+           "--steps", str(steps), "--warmup", str(warmup), "--rel-tol", str(args.rel_tol)]
+    if args.dims:
+        cmd += ["--dims", args.dims]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    _, dims, _ = workload(args)
+    ne_full = dims[0] * dims[1] * dims[2]
+    s = res["sample_dims"]
+    scale = ne_full / (s[0] * s[1] * s[2])
+    t = statistics.mean(res["times"])
+    return {
+        "value": t * scale,
+        "unit": "s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"oracle FP64 state solve (assembled CSR K, Galerkin-MG PCG to rel. residual {args.rel_tol:g}, "
+                   f"{res['iters']} it) of the same recipe on a {s[0]}x{s[1]}x{s[2]} grid: "
+                   f"{t:.2f} s, scaled by element count x{scale:.0f} to {dims[0]}x{dims[1]}x{dims[2]}"),
+    }
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def roofline(grid, nn, ne):
+    """Dominant fine-level operator kernel from the live event records."""
+    names = {0: "K.u", 1: "Jacobi sweep", 2: "residual", 3: "first Jacobi sweep"}
+    best = None
+    for mode in range(4):
+        cnt, ms = grid.profile_read(mode)
+        for prec in (0, 1):
+            if cnt[prec] and (best is None or ms[prec] > best[3]):
+                best = (mode, prec, cnt[prec], ms[prec])
+    if best is None:
+        return None
+    mode, prec, cnt, ms = best
+    s = 8 if prec == 0 else 4
+    vec = 3 * nn * s
+    nvec = {0: 2, 1: 3, 2: 3, 3: 2}[mode]
+    bytes_per_launch = nvec * vec + ne * s
+    avg_s = ms / cnt / 1e3
+    achieved = bytes_per_launch / avg_s / 1e9
+    peak, src = peaks()
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": f"{names[mode]} ({'fp64' if prec == 0 else 'fp32'}) fine level",
+            "launches": cnt, "avg_launch_ms": round(ms / cnt, 4), "algorithmic_bytes_per_launch": bytes_per_launch,
+            "peak_source": src}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_2201_12931_gb300 import Params, TopoGrid, TOPO_FP64, TOPO_MIXED, TOPO_MIXED_BF16, TOPO_OK
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w, dims, levels = workload(args)
+    prec = {"fp64": TOPO_FP64, "mixed": TOPO_MIXED, "mixed_bf16": TOPO_MIXED_BF16}[w["precision"]]
+    nx, ny, nz = dims
+    ne, nn = nx * ny * nz, (nx + 1) * (ny + 1) * (nz + 1)
+    pb = synth.make_problem(args.workload, dims)
+    fixed_d = torch.tensor(pb.fixed, device=dev)
+    f_d = torch.tensor(pb.f, device=dev)
+    del pb
+    rmin = w.get("oc", {}).get("rmin", w["density"].get("rmin", 1.5))
+    move = w.get("oc", {}).get("move", 0.2)
+
+    g = TopoGrid(dims, Params(levels=levels, precision=prec))
+    rho0 = physical_density(g, args.workload, dims, dev)
+    volfrac = w.get("oc", {}).get("volfrac", float(rho0.mean()))
+    g.set_bc_loads(fixed_d, f_d)
+    dc = torch.empty(ne, dtype=torch.float64, device=dev)
+    xw = torch.empty(ne, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(record):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.set_density(rho0)
+        g.reset_solution()
+        _, res = g.solve(args.rel_tol, 20000)
+        e1.record(stream)
+        C, _ = g.compliance_and_sensitivity(dc)
+        xw.copy_(rho0)
+        ch = g.oc_update(rmin, move, volfrac, xw, dc)
+        e2.record(stream)
+        if record is not None:
+            record.append((e0, e1, e2, res, C, ch))
+        return res, C
+
+    for _ in range(args.warmup):
+        step(None)
+    rec = []
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    g.profile_enable(True)
+    launches0 = g.launch_count()
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(rec)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = g.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    g.profile_enable(False)
+    solve_s = [a.elapsed_time(b) / 1e3 for a, b, _, _, _, _ in rec]
+    step_s = [a.elapsed_time(c) / 1e3 for a, _, c, _, _, _ in rec]
+    roof = roofline(g, nn, ne)
+    res_last, C_mixed = rec[-1][3], rec[-1][4]
+    t_solve = statistics.mean(solve_s)
+    t_step = statistics.mean(step_s)
+    if world > 1:
+        tt = torch.tensor([t_solve, t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_solve, t_step = float(tt[0]), float(tt[1])
+
+    # end to end through the C-ABI from pinned host memory: H2D of the step's
+    # density, set_density + solve, D2H of the compliance
+    host_rho = rho0.cpu().pin_memory()
+    rho_dev = torch.empty_like(rho0)
+    e2e = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rho_dev.copy_(host_rho, non_blocking=True)
+        g.set_density(rho_dev)
+        g.reset_solution()
+        g.solve(args.rel_tol, 20000)
+        Cv, _ = g.compliance_and_sensitivity()
+        e2e.append(time.perf_counter() - t1)
+
+    out = {
+        "metric": "state-solve s & K·u HBM GB/s at 113M hex; mixed vs FP64 GPU at 1e-6 compliance",
+        "value": round(t_solve, 5),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_step * 1e3, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64" if prec != TOPO_FP64 else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload if not args.dims else f"{args.workload}@{nx}x{ny}x{nz}",
+                   "grid": f"{nx}x{ny}x{nz}", "elements": ne, "dofs": 3 * nn, "levels": levels,
+                   "rel_tol": args.rel_tol, "precision": w["precision"],
+                   "l2": "inputs larger than L2 (fine-level vectors >= 129 MB)" if 12 * nn > 129e6
+                   else "inputs smaller than L2 (no flush)"},
+        "solve": {"status": res_last.status, "inner_iters": res_last.iters, "outer_steps": res_last.outer_steps,
+                  "relres_fp64": res_last.relres, "compliance": C_mixed,
+                  "solve_s_per_step": [round(v, 5) for v in solve_s]},
+        "gpu_launches": launches,
+        "wall_s_timed": round(t_wall, 3),
+        "e2e": {"value": round(statistics.mean(e2e), 5), "unit": "s",
+                "h2d_bytes_per_step": ne * 8, "d2h_bytes_per_step": 8},
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if args.fp64_ref == "full" and prec != TOPO_FP64:
+        g64 = TopoGrid(dims, Params(levels=levels, precision=TOPO_FP64))
+        g64.set_bc_loads(fixed_d, f_d)
+        g64.set_density(rho0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, r64 = g64.solve(args.fp64_tol, 20000)
+        t64 = time.perf_counter() - t1
+        C64_tol, _ = g64.compliance_and_sensitivity()
+        _, r64b = g64.solve(1e-10, 20000)
+        C_ref, _ = g64.compliance_and_sensitivity()
+        out["fp64_gpu"] = {"solve_s": round(t64, 4), "rel_tol": args.fp64_tol, "iters": r64.iters,
+                           "status": r64.status, "compliance_rel_err": abs(C64_tol - C_ref) / abs(C_ref),
+                           "compliance_at_tol": C64_tol, "reference_compliance_1e-10": C_ref,
+                           "reference_status": r64b.status, "reference_iters": r64b.iters}
+        out["compliance_rel_err_mixed_vs_fp64_ref"] = abs(C_mixed - C_ref) / abs(C_ref)
+        out["mixed_speedup_vs_fp64"] = round(t64 / t_solve, 3)
+        g64.close()
+    if rank == 0 and args.cpu_baseline == "on":
+        try:
+            out["cpu_baseline"] = cpu_baseline(args)
+        except Exception as e:   # the bench line must still print
+            out["cpu_baseline"] = {"error": str(e)[-300:]}
+    g.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, dims, levels = workload(args)
+    cb = cpu_baseline(args, steps=args.steps, warmup=args.warmup)
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "state-solve s & K·u HBM GB/s at 113M hex; mixed vs FP64 GPU at 1e-6 compliance",
+        "value": cb["value"], "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": "x".join(map(str, dims)), "levels": levels,
+                   "rel_tol": args.rel_tol},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.cpu_child:
+        run_cpu_child(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+"""Thin Python wrapper over the C-ABI: torch CUDA tensors in, raw pointers out.
+
+PyTorch provides device memory and the stream; all arithmetic runs in the
+library's kernels.  Tensors must be contiguous CUDA tensors of the stated
+dtype; the wrapper checks shapes and dtypes and raises TopoError on any
+non-OK status (solves return TOPO_MAXITER in their result instead).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+class TopoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class Params:
+    E0: float = 1.0
+    Emin: float = 1e-9
+    nu: float = 0.3
+    penal: float = 3.0
+    levels: int = 3
+    pre: int = 2
+    post: int = 2
+    omega: float = 0.35
+    precision: int = L.TOPO_FP64
+    inner_tol: float = 1e-2
+    inner_max_it: int = 500
+    max_refine: int = 12
+
+    def to_c(self) -> L.TopoParams:
+        p = L.TopoParams()
+        for k in self.__dataclass_fields__:
+            setattr(p, k, getattr(self, k))
+        return p
+
+
+@dataclass
+class SolveResult:
+    status: int
+    iters: int
+    relres: float
+    outer_steps: int
+    solve_ms: float
+
+
+def _ptr(t: torch.Tensor, dtype, numel=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class TopoGrid:
+    """One structured grid with its solver workspace on the current CUDA device."""
+
+    def __init__(self, dims, params: Params | None = None, stream: torch.cuda.Stream | None = None):
+        self.lib = L.load()
+        self.dims = tuple(int(d) for d in dims)
+        self.params = params or Params()
+        nx, ny, nz = self.dims
+        self.ne = nx * ny * nz
+        self.nn = (nx + 1) * (ny + 1) * (nz + 1)
+        self.stream = stream or torch.cuda.current_stream()
+        self._h = C.c_void_p()
+        cp = self.params.to_c()
+        st = self.lib.topo_create_grid(nx, ny, nz, C.byref(cp), C.c_void_p(self.stream.cuda_stream), C.byref(self._h))
+        if st != L.TOPO_OK:
+            raise TopoError(st, self.lib.topo_last_error(None).decode())
+        self.generation = 0
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if self._h:
+            self.lib.topo_destroy_grid(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != L.TOPO_OK and st not in allow:
+            raise TopoError(st, self.lib.topo_last_error(self._h).decode())
+        return st
+
+    def _dev(self):
+        return torch.device("cuda", torch.cuda.current_device())
+
+    # -- hot path ----------------------------------------------------------
+    def set_density(self, rho: torch.Tensor):
+        self._check(self.lib.topo_set_density(self._h, _ptr(rho, torch.float64, self.ne, "rho")))
+        self.generation += 1
+
+    def set_bc_loads(self, fixed: torch.Tensor, f: torch.Tensor):
+        self._check(self.lib.topo_set_bc_loads(self._h, _ptr(fixed, torch.uint8, 3 * self.nn, "fixed"),
+                                               _ptr(f, torch.float64, 3 * self.nn, "f")))
+        self.generation += 1
+
+    def solve(self, rel_tol=1e-8, max_it=1000, out: torch.Tensor | None = None):
+        """Returns (u or None, SolveResult).  TOPO_MAXITER is reported, not raised."""
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        up = _ptr(out, torch.float64, 3 * self.nn, "out") if out is not None else None
+        st = self.lib.topo_solve_state(self._h, rel_tol, max_it, up, C.byref(it), C.byref(rr))
+        self._check(st, allow=(L.TOPO_MAXITER,))
+        self.generation += 1
+        s = self.stats()
+        return out, SolveResult(st, it.value, rr.value, s.outer_steps, s.solve_ms)
+
+    def compliance_and_sensitivity(self, dc: torch.Tensor | None = None):
+        Cv = C.c_double(0.0)
+        dp = _ptr(dc, torch.float64, self.ne, "dc") if dc is not None else None
+        self._check(self.lib.topo_compliance_and_sensitivity(self._h, C.byref(Cv), dp))
+        return Cv.value, dc
+
+    def filter(self, r: float, x: torch.Tensor, transpose=False, out: torch.Tensor | None = None):
+        out = torch.empty_like(x) if out is None else out
+        self._check(self.lib.topo_filter(self._h, float(r), _ptr(x, torch.float64, self.ne, "in"),
+                                         _ptr(out, torch.float64, self.ne, "out"), 1 if transpose else 0))
+        return out
+
+    def oc_update(self, r: float, move: float, volfrac: float, x: torch.Tensor, dc: torch.Tensor) -> float:
+        ch = C.c_double(0.0)
+        self._check(self.lib.topo_oc_update(self._h, float(r), float(move), float(volfrac),
+                                            _ptr(x, torch.float64, self.ne, "x"),
+                                            _ptr(dc, torch.float64, self.ne, "dc"), C.byref(ch)))
+        return ch.value
+
+    # -- step-level entry points --------------------------------------------
+    def level_dims(self, level: int):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.topo_level_dims(self._h, level, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def level_nodes(self, level: int):
+        nx, ny, nz = self.level_dims(level)
+        return (nx + 1) * (ny + 1) * (nz + 1)
+
+    def apply_operator(self, u, level=0, precision=L.TOPO_FP64):
+        y = torch.empty_like(u)
+        n = 3 * self.level_nodes(level)
+        self._check(self.lib.topo_apply_operator(self._h, level, precision, _ptr(u, torch.float64, n, "u"),
+                                                 _ptr(y, torch.float64, n, "y")))
+        return y
+
+    def jacobi_sweep(self, u, f, level=0, precision=L.TOPO_FP64):
+        y = torch.empty_like(u)
+        n = 3 * self.level_nodes(level)
+        self._check(self.lib.topo_jacobi_sweep(self._h, level, precision, _ptr(u, torch.float64, n, "u"),
+                                               _ptr(f, torch.float64, n, "f"), _ptr(y, torch.float64, n, "out")))
+        return y
+
+    def residual(self, u, f, level=0, precision=L.TOPO_FP64):
+        y = torch.empty_like(u)
+        n = 3 * self.level_nodes(level)
+        self._check(self.lib.topo_residual(self._h, level, precision, _ptr(u, torch.float64, n, "u"),
+                                           _ptr(f, torch.float64, n, "f"), _ptr(y, torch.float64, n, "r")))
+        return y
+
+    def restrict(self, fine, level=0):
+        nc = 3 * self.level_nodes(level + 1)
+        out = torch.empty(nc, dtype=torch.float64, device=fine.device)
+        self._check(self.lib.topo_restrict(self._h, level, _ptr(fine, torch.float64, 3 * self.level_nodes(level)),
+                                           _ptr(out, torch.float64, nc)))
+        return out
+
+    def prolong_add(self, coarse, fine, level=0):
+        self._check(self.lib.topo_prolong_add(self._h, level, _ptr(coarse, torch.float64, 3 * self.level_nodes(level + 1)),
+                                              _ptr(fine, torch.float64, 3 * self.level_nodes(level))))
+        return fine
+
+    def level_density(self, level: int):
+        nx, ny, nz = self.level_dims(level)
+        out = torch.empty(nx * ny * nz, dtype=torch.float64, device=self._dev())
+        self._check(self.lib.topo_level_density(self._h, level, _ptr(out, torch.float64)))
+        return out
+
+    def vcycle(self, r, precision=L.TOPO_FP64):
+        z = torch.empty_like(r)
+        self._check(self.lib.topo_vcycle(self._h, precision, _ptr(r, torch.float64, 3 * self.nn, "r"),
+                                         _ptr(z, torch.float64, 3 * self.nn, "z")))
+        return z
+
+    def stats(self) -> L.TopoSolveStats:
+        s = L.TopoSolveStats()
+        self._check(self.lib.topo_get_stats(self._h, C.byref(s)))
+        return s
+
+    def reset_solution(self):
+        self._check(self.lib.topo_reset_solution(self._h))
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.topo_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, mode: int):
+        """(launches, total_ms) per precision [fp64, fp32] for operator kind `mode`."""
+        n = (C.c_longlong * 2)()
+        ms = (C.c_double * 2)()
+        self._check(self.lib.topo_profile_read(self._h, mode, n, ms))
+        return [n[0], n[1]], [ms[0], ms[1]]
+
+    def launch_count(self) -> int:
+        v = C.c_longlong(0)
+        self._check(self.lib.topo_launch_count(self._h, C.byref(v)))
+        return v.value

@@ -1,0 +1,383 @@
+// Vector kernels of the CG loop (Algorithm 1: dots, alpha/beta, x/r/p updates;
+// all on the device, no host round trip per iteration) and the dense direct
+// solve on the coarsest grid (Algorithm 3 "Solve the problem directly"):
+// blocked right-looking Cholesky K_c = L L^T, explicit W = L^-1, and per
+// application u = W^T (W r) as two triangular matrix-vector products.
+// Reductions use a fixed grid of kRedBlocks blocks and a fixed-order second
+// pass, so results are bitwise reproducible run to run.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace topo {
+
+namespace {
+
+constexpr int TB = 32;   // dense tile
+
+inline unsigned grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+template <typename A, typename B>
+__global__ void __launch_bounds__(256) k_dot(long long n, const A* __restrict__ a, const B* __restrict__ b,
+                                             double* __restrict__ partials) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__device__ __forceinline__ double sum_partials(const double* __restrict__ p, double* sh) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) s += p[i];
+    return block_sum(s, sh);
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_to(const double* __restrict__ p, double* dst) {
+    __shared__ double sh[32];
+    const double s = sum_partials(p, sh);
+    if (threadIdx.x == 0) *dst = s;
+}
+
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p, Scalars* sc) {
+    __shared__ double sh[32];
+    const double pq = sum_partials(p, sh);
+    if (threadIdx.x == 0) {
+        sc->pq = pq;
+        if (pq > 0.0 && isfinite(pq) && isfinite(sc->rz)) {
+            sc->alpha = sc->rz / pq;
+        } else {
+            sc->alpha = 0.0;
+            sc->aux = 1.0;   // breakdown flag, read by the host
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_cg_beta(const double* __restrict__ p, Scalars* sc) {
+    __shared__ double sh[32];
+    const double rz = sum_partials(p, sh);
+    if (threadIdx.x == 0) {
+        const double old = sc->rz;
+        sc->rz_new = rz;
+        sc->beta = (old != 0.0 && isfinite(rz)) ? rz / old : 0.0;
+        if (!isfinite(rz)) sc->aux = 1.0;
+        sc->rz = rz;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_xr(long long n, const Scalars* __restrict__ sc, const T* __restrict__ p,
+                                                   const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
+                                                   double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const T a = (T)sc->alpha;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        const T ri = r[i] - a * q[i];
+        r[i] = ri;
+        s += (double)ri * (double)ri;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_update_p(long long n, const Scalars* __restrict__ sc, const T* __restrict__ z, T* __restrict__ p) {
+    const T b = (T)sc->beta;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
+template <typename S, typename D>
+__global__ void k_convert(long long n, const S* __restrict__ s, D* __restrict__ d) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        d[i] = (D)s[i];
+}
+
+__global__ void k_fill(long long n, double* __restrict__ v, double value) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[i] = value;
+}
+
+__global__ void k_axpy_f32(long long n, const float* __restrict__ d, double* __restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+// ---- dense coarse solve --------------------------------------------------
+
+__global__ void k_potrf_diag(double* __restrict__ A, int npad, int kb, int* info) {
+    __shared__ double s[TB][TB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long base = (long long)kb * TB;
+    s[ty][tx] = A[(base + ty) * npad + base + tx];
+    for (int j = 0; j < TB; ++j) {
+        __syncthreads();
+        if (ty == j && tx == j) {
+            double d = s[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                atomicCAS(info, 0, (int)(base + j) + 1);
+                d = 1.0;
+            }
+            s[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (tx == j && ty > j) s[ty][j] /= s[j][j];
+        __syncthreads();
+        if (tx > j && ty >= tx) s[ty][tx] -= s[ty][j] * s[tx][j];
+    }
+    __syncthreads();
+    A[(base + ty) * npad + base + tx] = (tx <= ty) ? s[ty][tx] : 0.0;
+}
+
+// L_ib,kb = A_ib,kb L_kk^-T for every block row ib > kb (one block each)
+__global__ void k_trsm_panel(double* __restrict__ A, int npad, int kb) {
+    __shared__ double sL[TB][TB + 1];
+    __shared__ double sA[TB][TB + 1];
+    const int ib = kb + 1 + blockIdx.x;
+    const int r = threadIdx.x;
+    const long long rb = (long long)ib * TB, cb = (long long)kb * TB;
+    for (int c = 0; c < TB; ++c) {
+        sL[r][c] = A[(cb + r) * npad + cb + c];
+        sA[r][c] = A[(rb + r) * npad + cb + c];
+    }
+    __syncwarp();
+    for (int j = 0; j < TB; ++j) {
+        double v = sA[r][j];
+        for (int c = 0; c < j; ++c) v -= sA[r][c] * sL[j][c];
+        sA[r][j] = v / sL[j][j];
+    }
+    for (int c = 0; c < TB; ++c) A[(rb + r) * npad + cb + c] = sA[r][c];
+}
+
+// A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib
+__global__ void k_syrk(double* __restrict__ A, int npad, int kb) {
+    __shared__ double sI[TB][TB + 1];
+    __shared__ double sJ[TB][TB + 1];
+    const int t = blockIdx.x;
+    int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+    while (ii * (ii + 1) / 2 > t) --ii;
+    const int jj = t - ii * (ii + 1) / 2;
+    const int ib = kb + 1 + ii, jb = kb + 1 + jj;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long cb = (long long)kb * TB;
+    sI[ty][tx] = A[((long long)ib * TB + ty) * npad + cb + tx];
+    sJ[ty][tx] = A[((long long)jb * TB + ty) * npad + cb + tx];
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < TB; ++c) s += sI[ty][c] * sJ[tx][c];
+    A[((long long)ib * TB + ty) * npad + (long long)jb * TB + tx] -= s;
+}
+
+__global__ void k_identity(double* __restrict__ W, int npad) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n2 = (long long)npad * npad;
+    if (i >= n2) return;
+    W[i] = ((i / npad) == (i % npad)) ? 1.0 : 0.0;
+}
+
+// W_kb,jb = L_kk^-1 B_kb,jb for jb <= kb (forward substitution, thread per column)
+__global__ void k_trsm_rows(const double* __restrict__ L, double* __restrict__ W, int npad, int kb) {
+    __shared__ double sL[TB][TB + 1];
+    const int jb = blockIdx.x;
+    const int col = threadIdx.x;
+    const long long rb = (long long)kb * TB;
+    for (int r = 0; r < TB; ++r) sL[r][col] = L[(rb + r) * npad + rb + col];
+    __syncwarp();
+    double x[TB];
+#pragma unroll
+    for (int r = 0; r < TB; ++r) x[r] = W[(rb + r) * npad + (long long)jb * TB + col];
+#pragma unroll
+    for (int r = 0; r < TB; ++r) {
+        double v = x[r];
+#pragma unroll
+        for (int c = 0; c < r; ++c) v -= sL[r][c] * x[c];
+        x[r] = v / sL[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < TB; ++r) W[(rb + r) * npad + (long long)jb * TB + col] = x[r];
+}
+
+// B_ib,jb -= L_ib,kb W_kb,jb for ib > kb, jb <= kb
+__global__ void k_gemm_update(const double* __restrict__ L, double* __restrict__ W, int npad, int kb) {
+    __shared__ double sL[TB][TB + 1];
+    __shared__ double sW[TB][TB + 1];
+    const int ib = kb + 1 + blockIdx.y, jb = blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long kbase = (long long)kb * TB;
+    sL[ty][tx] = L[((long long)ib * TB + ty) * npad + kbase + tx];
+    sW[ty][tx] = W[(kbase + ty) * npad + (long long)jb * TB + tx];
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < TB; ++c) s += sL[ty][c] * sW[c][tx];
+    W[((long long)ib * TB + ty) * npad + (long long)jb * TB + tx] -= s;
+}
+
+__global__ void k_transpose(const double* __restrict__ W, double* __restrict__ WT, int npad) {
+    __shared__ double s[TB][TB + 1];
+    const int bx = blockIdx.x, by = blockIdx.y, tx = threadIdx.x, ty = threadIdx.y;
+    s[ty][tx] = W[((long long)by * TB + ty) * npad + (long long)bx * TB + tx];
+    __syncthreads();
+    WT[((long long)bx * TB + ty) * npad + (long long)by * TB + tx] = s[tx][ty];
+}
+
+// y_i = sum_{j<=i} W_ij r_j  (lower) or sum_{j>=i} (upper); warp per row
+template <typename T, bool LOWER>
+__global__ void k_trigemv(int n, int npad, const T* __restrict__ M, const T* __restrict__ v, T* __restrict__ y) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int j0 = LOWER ? 0 : row, j1 = LOWER ? row + 1 : n;
+    double s = 0.0;
+    const T* mr = M + (long long)row * npad;
+    for (int j = j0 + lane; j < j1; j += 32) s += (double)mr[j] * (double)v[j];
+    s = warp_sum(s);
+    if (lane == 0) y[row] = (T)s;
+}
+
+}  // namespace
+
+template <typename A, typename B>
+void dot_partials(const Ctx& c, long long n, const A* a, const B* b, double* partials) {
+    k_dot<A, B><<<kRedBlocks, 256, 0, c.s>>>(n, a, b, partials);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void dot_partials<double, double>(const Ctx&, long long, const double*, const double*, double*);
+template void dot_partials<float, float>(const Ctx&, long long, const float*, const float*, double*);
+template void dot_partials<double, float>(const Ctx&, long long, const double*, const float*, double*);
+
+void reduce_to(const Ctx& c, const double* partials, double* dst) {
+    k_reduce_to<<<1, 1024, 0, c.s>>>(partials, dst);
+    TOPO_LAUNCH_CHECK(c);
+}
+void cg_alpha(const Ctx& c, const double* partials, Scalars* sc) {
+    k_cg_alpha<<<1, 1024, 0, c.s>>>(partials, sc);
+    TOPO_LAUNCH_CHECK(c);
+}
+void cg_beta(const Ctx& c, const double* partials, Scalars* sc) {
+    k_cg_beta<<<1, 1024, 0, c.s>>>(partials, sc);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+template <typename T>
+void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, const T* q, T* x, T* r,
+                  double* partials) {
+    k_update_xr<T><<<kRedBlocks, 256, 0, c.s>>>(n, sc, p, q, x, r, partials);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void cg_update_xr<double>(const Ctx&, long long, const Scalars*, const double*, const double*, double*,
+                                   double*, double*);
+template void cg_update_xr<float>(const Ctx&, long long, const Scalars*, const float*, const float*, float*, float*,
+                                  double*);
+
+template <typename T>
+void cg_update_p(const Ctx& c, long long n, const Scalars* sc, const T* z, T* p) {
+    k_update_p<T><<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, sc, z, p);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void cg_update_p<double>(const Ctx&, long long, const Scalars*, const double*, double*);
+template void cg_update_p<float>(const Ctx&, long long, const Scalars*, const float*, float*);
+
+template <typename S, typename D>
+void convert(const Ctx& c, long long n, const S* src, D* dst) {
+    k_convert<S, D><<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, src, dst);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void convert<double, float>(const Ctx&, long long, const double*, float*);
+template void convert<float, double>(const Ctx&, long long, const float*, double*);
+
+void axpy_f32_into_f64(const Ctx& c, long long n, const float* d, double* x) {
+    k_axpy_f32<<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, d, x);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+template <typename T>
+void zero(const Ctx& c, long long n, T* v) {
+    cudaMemsetAsync(v, 0, sizeof(T) * (size_t)n, c.s);
+}
+template void zero<double>(const Ctx&, long long, double*);
+template void zero<float>(const Ctx&, long long, float*);
+
+void fill(const Ctx& c, long long n, double* v, double value) {
+    k_fill<<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, v, value);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void chol_factor(const Ctx& c, double* A, int npad, int* info) {
+    const int nb = npad / TB;
+    cudaMemsetAsync(info, 0, sizeof(int), c.s);
+    for (int kb = 0; kb < nb; ++kb) {
+        k_potrf_diag<<<1, dim3(TB, TB), 0, c.s>>>(A, npad, kb, info);
+        TOPO_LAUNCH_CHECK(c);
+        const int m = nb - kb - 1;
+        if (m > 0) {
+            k_trsm_panel<<<m, TB, 0, c.s>>>(A, npad, kb);
+            TOPO_LAUNCH_CHECK(c);
+            k_syrk<<<m * (m + 1) / 2, dim3(TB, TB), 0, c.s>>>(A, npad, kb);
+            TOPO_LAUNCH_CHECK(c);
+        }
+    }
+}
+
+void tri_inverse(const Ctx& c, const double* L, double* W, int npad) {
+    const int nb = npad / TB;
+    const long long n2 = (long long)npad * npad;
+    k_identity<<<grid_for(n2, 256), 256, 0, c.s>>>(W, npad);
+    TOPO_LAUNCH_CHECK(c);
+    for (int kb = 0; kb < nb; ++kb) {
+        k_trsm_rows<<<kb + 1, TB, 0, c.s>>>(L, W, npad, kb);
+        TOPO_LAUNCH_CHECK(c);
+        const int m = nb - kb - 1;
+        if (m > 0) {
+            k_gemm_update<<<dim3(kb + 1, m), dim3(TB, TB), 0, c.s>>>(L, W, npad, kb);
+            TOPO_LAUNCH_CHECK(c);
+        }
+    }
+}
+
+void transpose_dense(const Ctx& c, const double* W, double* WT, int npad) {
+    const int nb = npad / TB;
+    k_transpose<<<dim3(nb, nb), dim3(TB, TB), 0, c.s>>>(W, WT, npad);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+template <typename T>
+void coarse_apply(const Ctx& c, int n, int npad, const T* W, const T* WT, const T* rhs, T* y, T* out) {
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    k_trigemv<T, true><<<blocks, 256, 0, c.s>>>(n, npad, W, rhs, y);
+    TOPO_LAUNCH_CHECK(c);
+    k_trigemv<T, false><<<blocks, 256, 0, c.s>>>(n, npad, WT, y, out);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void coarse_apply<double>(const Ctx&, int, int, const double*, const double*, const double*, double*,
+                                   double*);
+template void coarse_apply<float>(const Ctx&, int, int, const float*, const float*, const float*, float*, float*);
+
+}  // namespace topo

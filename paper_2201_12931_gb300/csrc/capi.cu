@@ -1,0 +1,669 @@
+// extern "C" entry points of include/topo.h: argument checks, device
+// workspace, per-level set-up (Sec. 4.2.2 homogenization), and dispatch to the
+// solver and the element / filter / OC kernels.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.h"
+
+using namespace topo;
+
+namespace {
+
+std::string g_create_err;
+constexpr int kMaxCoarseDofs = 12000;
+
+topo_status fail(topo_grid* h, topo_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), TOPO_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+topo_status dalloc(topo_grid* h, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(h, e == cudaErrorMemoryAllocation ? TOPO_OOM : TOPO_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(sizeof(T) * n) + " bytes): " + cudaGetErrorString(e));
+    }
+    return TOPO_OK;
+}
+
+#define ALLOC(h, p, n)                               \
+    do {                                             \
+        topo_status s_ = dalloc((h), &(p), (n));     \
+        if (s_ != TOPO_OK) return s_;                \
+    } while (0)
+
+// K0 of the unit cube by 2x2x2 Gauss quadrature of B^T D B (isotropic, E = 1).
+// Local corner a = ax + 2 ay + 4 az, DOF 3 a + c.
+void element_matrix(double nu, double K[576]) {
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+    double D[6][6] = {};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) D[i][j] = lam + (i == j ? 2.0 * mu : 0.0);
+    D[3][3] = D[4][4] = D[5][5] = mu;
+    const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+    std::memset(K, 0, sizeof(double) * 576);
+    for (int q = 0; q < 8; ++q) {
+        const double x = gp[q & 1], y = gp[(q >> 1) & 1], z = gp[q >> 2];
+        double B[6][24] = {};
+        for (int a = 0; a < 8; ++a) {
+            const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+            const double lx = ax ? x : 1.0 - x, ly = ay ? y : 1.0 - y, lz = az ? z : 1.0 - z;
+            const double sx = ax ? 1.0 : -1.0, sy = ay ? 1.0 : -1.0, sz = az ? 1.0 : -1.0;
+            const double dx = sx * ly * lz, dy = lx * sy * lz, dz = lx * ly * sz;
+            B[0][3 * a] = dx;
+            B[1][3 * a + 1] = dy;
+            B[2][3 * a + 2] = dz;
+            B[3][3 * a] = dy;
+            B[3][3 * a + 1] = dx;
+            B[4][3 * a + 1] = dz;
+            B[4][3 * a + 2] = dy;
+            B[5][3 * a] = dz;
+            B[5][3 * a + 2] = dx;
+        }
+        double DB[6][24];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 24; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += D[i][k] * B[k][j];
+                DB[i][j] = s;
+            }
+        for (int i = 0; i < 24; ++i)
+            for (int j = 0; j < 24; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 6; ++k) s += B[k][i] * DB[k][j];
+                K[i * 24 + j] += 0.125 * s;
+            }
+    }
+}
+
+Geom make_geom(int nx, int ny, int nz) {
+    Geom g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    g.ne = (long long)nx * ny * nz;
+    return g;
+}
+
+topo_status alloc_precision(topo_grid* h, bool fp64) {
+    if (fp64 && h->fp64_ready) return TOPO_OK;
+    if (!fp64 && h->fp32_ready) return TOPO_OK;
+    const long long n0 = 3 * h->lev[0].g.nn;
+    for (int l = 0; l < h->L; ++l) {
+        const long long n = 3 * h->lev[l].g.nn;
+        if (fp64) {
+            ALLOC(h, h->lev[l].v64.a, n);
+            ALLOC(h, h->lev[l].v64.b, n);
+            ALLOC(h, h->lev[l].v64.f, n);
+        } else {
+            ALLOC(h, h->lev[l].v32.a, n);
+            ALLOC(h, h->lev[l].v32.b, n);
+            ALLOC(h, h->lev[l].v32.f, n);
+        }
+    }
+    if (fp64) {
+        ALLOC(h, h->z, n0);
+        ALLOC(h, h->p, n0);
+        ALLOC(h, h->q, n0);
+        h->fp64_ready = true;
+    } else {
+        ALLOC(h, h->r32, n0);
+        ALLOC(h, h->z32, n0);
+        ALLOC(h, h->p32, n0);
+        ALLOC(h, h->q32, n0);
+        ALLOC(h, h->d32, n0);
+        h->fp32_ready = true;
+    }
+    return TOPO_OK;
+}
+
+void free_all(topo_grid* h) {
+    auto F = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    for (auto& l : h->lev) {
+        F(l.rho); F(l.E64); F(l.E32); F(l.mask);
+        F(l.v64.a); F(l.v64.b); F(l.v64.f);
+        F(l.v32.a); F(l.v32.b); F(l.v32.f);
+    }
+    F(h->cs.A); F(h->cs.W64); F(h->cs.WT64); F(h->cs.W32); F(h->cs.WT32); F(h->cs.y64); F(h->cs.y32);
+    F(h->cs.info);
+    F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
+    F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
+    F(h->K0d); F(h->K0f);
+    F(h->dc_work); F(h->dv_work); F(h->xnew_work); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
+    F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
+    if (h->host_sc) cudaFreeHost(h->host_sc);
+    for (auto e : h->prof_ev) cudaEventDestroy(e);
+    h->prof_ev.clear();
+}
+
+// The dense coarsest-grid workspace is allocated on first use, so that handles
+// used only for filtering or single-level operators need no coarse factor.
+topo_status ensure_coarse(topo_grid* h) {
+    if (!h->coarse_dirty) return TOPO_OK;
+    if (!h->have_density || !h->have_bc) return fail(h, TOPO_BADARG, "density and boundary conditions must be set");
+    const Ctx c = h->ctx();
+    Level& lc = h->lev[h->L - 1];
+    Coarse& cs = h->cs;
+    if (cs.n > kMaxCoarseDofs)
+        return fail(h, TOPO_BADARG, "coarsest grid has " + std::to_string(cs.n) + " DOFs (> " +
+                                        std::to_string(kMaxCoarseDofs) + "): use more levels");
+    if (!cs.A) {
+        const size_t n2 = (size_t)cs.npad * cs.npad;
+        ALLOC(h, cs.A, n2);
+        ALLOC(h, cs.W64, n2);
+        ALLOC(h, cs.WT64, n2);
+        ALLOC(h, cs.W32, n2);
+        ALLOC(h, cs.WT32, n2);
+        ALLOC(h, cs.y64, cs.npad);
+        ALLOC(h, cs.y32, cs.npad);
+        ALLOC(h, cs.info, 1);
+    }
+    assemble_coarse(c, lc.g, h->K0d, lc.E64, lc.mask, cs.A, cs.npad);
+    chol_factor(c, cs.A, cs.npad, cs.info);
+    int info = 0;
+    CK(h, cudaMemcpyAsync(&info, cs.info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (info != 0)
+        return fail(h, TOPO_BREAKDOWN, "coarsest-grid matrix not positive definite at row " + std::to_string(info - 1));
+    tri_inverse(c, cs.A, cs.W64, cs.npad);
+    transpose_dense(c, cs.W64, cs.WT64, cs.npad);
+    const long long n2 = (long long)cs.npad * cs.npad;
+    convert<double, float>(c, n2, cs.W64, cs.W32);
+    convert<double, float>(c, n2, cs.WT64, cs.WT32);
+    h->coarse_dirty = false;
+    return TOPO_OK;
+}
+
+topo_status prepare_filter(topo_grid* h, double r) {
+    if (!(r > 0.0) || r > 6.0) return fail(h, TOPO_BADARG, "filter radius must be in (0, 6]");
+    if (r == h->S_radius) return TOPO_OK;
+    const int R = (int)std::ceil(r);
+    std::vector<int4> offs;
+    std::vector<double> wts;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                const double w = r - std::sqrt((double)(dx * dx + dy * dy + dz * dz));
+                if (w > 0.0) {
+                    offs.push_back(make_int4(dx, dy, dz, 0));
+                    wts.push_back(w);
+                }
+            }
+    if (h->offs) cudaFree(h->offs);
+    if (h->wts) cudaFree(h->wts);
+    h->offs = nullptr;
+    h->wts = nullptr;
+    ALLOC(h, h->offs, offs.size());
+    ALLOC(h, h->wts, wts.size());
+    CK(h, cudaMemcpyAsync(h->offs, offs.data(), sizeof(int4) * offs.size(), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->wts, wts.data(), sizeof(double) * wts.size(), cudaMemcpyHostToDevice, h->stream));
+    h->noffs = (int)offs.size();
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    filter_launch(c, g, h->offs, h->wts, h->noffs, nullptr, h->S_cache, 2, nullptr);
+    fill(c, g.ne, h->xnew_work, 1.0);
+    filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dv_cache, 1, h->S_cache);
+    CK(h, cudaStreamSynchronize(h->stream));   // host vectors above go out of scope
+    h->S_radius = r;
+    return TOPO_OK;
+}
+
+topo_status check_handle(topo_grid* h) {
+    if (!h) return TOPO_BADARG;
+    h->err.clear();
+    CK(h, cudaSetDevice(h->device));
+    return TOPO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+topo_status topo_default_params(topo_params* p) {
+    if (!p) return TOPO_BADARG;
+    p->E0 = 1.0;
+    p->Emin = 1e-9;
+    p->nu = 0.3;
+    p->penal = 3.0;
+    p->levels = 3;
+    p->pre = 2;
+    p->post = 2;
+    p->omega = 0.35;
+    p->precision = TOPO_FP64;
+    p->inner_tol = 1e-2;
+    p->inner_max_it = 500;
+    p->max_refine = 12;
+    return TOPO_OK;
+}
+
+topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, void* stream, topo_handle* out) {
+    if (!out) return fail(nullptr, TOPO_BADARG, "out is NULL");
+    *out = nullptr;
+    if (!prm) return fail(nullptr, TOPO_BADARG, "params is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(nullptr, TOPO_BADARG, "grid dimensions must be positive");
+    const topo_params& p = *prm;
+    if (p.levels < 1 || p.levels > 16) return fail(nullptr, TOPO_BADARG, "levels must be in [1, 16]");
+    const int div = 1 << (p.levels - 1);
+    if (nx % div || ny % div || nz % div)
+        return fail(nullptr, TOPO_BADARG, "grid dimensions must be divisible by 2^(levels-1) = " + std::to_string(div));
+    if (!(p.nu >= 0.0 && p.nu < 0.5)) return fail(nullptr, TOPO_BADARG, "nu must be in [0, 0.5)");
+    if (!(p.E0 > 0.0) || !(p.Emin >= 0.0) || !(p.Emin < p.E0)) return fail(nullptr, TOPO_BADARG, "need 0 <= Emin < E0");
+    if (!(p.penal >= 1.0 && p.penal <= 10.0)) return fail(nullptr, TOPO_BADARG, "penal must be in [1, 10]");
+    if (!(p.omega > 0.0 && p.omega <= 1.0)) return fail(nullptr, TOPO_BADARG, "omega must be in (0, 1]");
+    if (p.pre < 0 || p.post < 0 || p.pre > 32 || p.post > 32) return fail(nullptr, TOPO_BADARG, "bad sweep counts");
+    if (p.precision < TOPO_FP64 || p.precision > TOPO_MIXED_BF16) return fail(nullptr, TOPO_BADARG, "bad precision");
+    if (!(p.inner_tol > 0.0 && p.inner_tol < 1.0) || p.inner_max_it < 1 || p.max_refine < 1)
+        return fail(nullptr, TOPO_BADARG, "bad inner solver parameters");
+    if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))
+        return fail(nullptr, TOPO_BADARG, "grid too large");
+
+    topo_grid* h = new (std::nothrow) topo_grid();
+    if (!h) return fail(nullptr, TOPO_OOM, "host allocation failed");
+    h->prm = p;
+    h->stream = (cudaStream_t)stream;
+    h->L = p.levels;
+    auto bail = [&](topo_status st) {
+        g_create_err = h->err;
+        free_all(h);
+        delete h;
+        return st;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        h->err = "no CUDA device";
+        return bail(TOPO_CUDA);
+    }
+    double K0[576];
+    element_matrix(p.nu, K0);
+    if (!build_modal(K0, &h->modal, &h->err)) return bail(TOPO_BADARG);
+    h->lev.resize(h->L);
+    for (int l = 0; l < h->L; ++l) {
+        Level& lv = h->lev[l];
+        lv.g = make_geom(nx >> l, ny >> l, nz >> l);
+        lv.scale = (double)(1 << l);
+    }
+    topo_status st;
+#define TRY(expr)                          \
+    do {                                   \
+        st = (expr);                       \
+        if (st != TOPO_OK) return bail(st); \
+    } while (0)
+    for (auto& lv : h->lev) {
+        TRY(dalloc(h, &lv.rho, lv.g.ne));
+        TRY(dalloc(h, &lv.E64, lv.g.ne));
+        TRY(dalloc(h, &lv.E32, lv.g.ne));
+        TRY(dalloc(h, &lv.mask, lv.g.nn));
+    }
+    const Geom& g0 = h->lev[0].g;
+    const long long n0 = 3 * g0.nn;
+    TRY(dalloc(h, &h->x, n0));
+    TRY(dalloc(h, &h->f, n0));
+    TRY(dalloc(h, &h->r, n0));
+    TRY(dalloc(h, &h->K0d, 576));
+    TRY(dalloc(h, &h->K0f, 576));
+    TRY(dalloc(h, &h->dc_work, g0.ne));
+    TRY(dalloc(h, &h->xnew_work, g0.ne));
+    TRY(dalloc(h, &h->S_cache, g0.ne));
+    TRY(dalloc(h, &h->dv_cache, g0.ne));
+    TRY(dalloc(h, &h->lam, 8));
+    TRY(dalloc(h, &h->dtmp, 8));
+    TRY(dalloc(h, &h->dflag, 4));
+    TRY(dalloc(h, &h->partials, kRedBlocks));
+    TRY(dalloc(h, &h->sc, 1));
+    h->cs.n = (int)std::min<long long>(3 * h->lev[h->L - 1].g.nn, 1LL << 30);
+    h->cs.npad = (h->cs.n + 31) / 32 * 32;
+    TRY(alloc_precision(h, p.precision == TOPO_FP64));
+    if (cudaMallocHost((void**)&h->host_sc, sizeof(Scalars)) != cudaSuccess) {
+        h->host_sc = nullptr;
+        h->err = "cudaMallocHost failed";
+        return bail(TOPO_OOM);
+    }
+    std::memset(h->host_sc, 0, sizeof(Scalars));
+    float K0f[576];
+    for (int i = 0; i < 576; ++i) K0f[i] = (float)K0[i];
+    bool ok = cudaMemcpyAsync(h->K0d, K0, sizeof(K0), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemcpyAsync(h->K0f, K0f, sizeof(K0f), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
+              cudaMemsetAsync(h->x, 0, sizeof(double) * n0, h->stream) == cudaSuccess &&
+              cudaMemsetAsync(h->f, 0, sizeof(double) * n0, h->stream) == cudaSuccess &&
+              cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream) == cudaSuccess &&
+              cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) == cudaSuccess;
+    for (auto& lv : h->lev) ok = ok && cudaMemsetAsync(lv.mask, 0, lv.g.nn, h->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;   // K0 host arrays go out of scope
+    if (!ok) {
+        h->err = std::string("initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+        return bail(TOPO_CUDA);
+    }
+#undef TRY
+    *out = h;
+    return TOPO_OK;
+}
+
+topo_status topo_destroy_grid(topo_handle h) {
+    if (!h) return TOPO_BADARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return TOPO_OK;
+}
+
+const char* topo_last_error(topo_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+topo_status topo_set_density(topo_handle h, const double* rho_dev) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev) return fail(h, TOPO_BADARG, "rho is NULL");
+    const Ctx c = h->ctx();
+    CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
+    CK(h, cudaMemcpyAsync(h->lev[0].rho, rho_dev, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToDevice, h->stream));
+    for (int l = 0; l < h->L; ++l) {
+        Level& lv = h->lev[l];
+        simp_moduli(c, lv.g.ne, lv.rho, lv.scale, h->prm.E0, h->prm.Emin, h->prm.penal, lv.E64, lv.E32, h->dflag);
+        if (l + 1 < h->L) homogenize(c, lv.g, lv.rho, h->lev[l + 1].rho);
+    }
+    CK(h, cudaGetLastError());
+    h->have_density = true;
+    h->coarse_dirty = true;
+    return TOPO_OK;
+}
+
+topo_status topo_set_bc_loads(topo_handle h, const uint8_t* fixed_dev, const double* f_dev) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!fixed_dev || !f_dev) return fail(h, TOPO_BADARG, "NULL pointer");
+    const Ctx c = h->ctx();
+    mask_from_dofs(c, h->lev[0].g.nn, fixed_dev, h->lev[0].mask);
+    for (int l = 0; l + 1 < h->L; ++l) inject_mask(c, h->lev[l].g, h->lev[l].mask, h->lev[l + 1].mask);
+    const long long n0 = 3 * h->lev[0].g.nn;
+    masked_copy_load(c, h->lev[0].g.nn, h->lev[0].mask, f_dev, h->f);
+    CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * n0, h->stream));
+    dot_partials<double, double>(c, n0, h->f, h->f, h->partials);
+    reduce_to(c, h->partials, &h->sc->ff);
+    CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->have_bc = true;
+    h->coarse_dirty = true;
+    return TOPO_OK;
+}
+
+topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it, double* u_dev_out, int* iters_out,
+                             double* relres_out) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!(rel_tol > 0.0) || max_it < 1) return fail(h, TOPO_BADARG, "rel_tol must be > 0 and max_it >= 1");
+    if (!h->have_density || !h->have_bc) return fail(h, TOPO_BADARG, "set density and boundary conditions first");
+    const auto t0 = std::chrono::steady_clock::now();
+    int bad = 0;
+    CK(h, cudaMemcpyAsync(&bad, h->dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, TOPO_BADARG, "density outside [0, 1] or NaN");
+    const bool fp64 = h->prm.precision == TOPO_FP64;
+    s = alloc_precision(h, fp64);
+    if (s != TOPO_OK) return s;
+    s = ensure_coarse(h);
+    if (s != TOPO_OK) return s;
+    int iters = 0;
+    double relres = 0.0;
+    int st = TOPO_OK;
+    const double ff = h->host_sc[6];
+    if (ff == 0.0) {
+        CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * 3 * h->lev[0].g.nn, h->stream));
+        h->stats.outer_steps = 0;
+    } else if (fp64) {
+        st = solve_fp64(h, rel_tol, max_it, &iters, &relres);
+    } else {
+        st = solve_mixed(h, rel_tol, max_it, &iters, &relres);
+    }
+    if (u_dev_out)
+        CK(h, cudaMemcpyAsync(u_dev_out, h->x, sizeof(double) * 3 * h->lev[0].g.nn, cudaMemcpyDeviceToDevice,
+                              h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    const auto t1 = std::chrono::steady_clock::now();
+    h->stats.inner_iters = iters;
+    h->stats.relres = relres;
+    h->stats.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    h->stats.status = st;
+    if (iters_out) *iters_out = iters;
+    if (relres_out) *relres_out = relres;
+    if (st == TOPO_MAXITER) h->err = "solver did not reach the tolerance";
+    if (st == TOPO_BREAKDOWN) h->err = "CG breakdown (non-positive curvature or non-finite value)";
+    return (topo_status)st;
+}
+
+topo_status topo_compliance_and_sensitivity(topo_handle h, double* C_out, double* dc_dev_out) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!h->have_density || !h->have_bc) return fail(h, TOPO_BADARG, "set density and boundary conditions first");
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    element_energy_sens(c, g, h->modal, h->x, h->lev[0].rho, h->prm.E0, h->prm.Emin, h->prm.penal,
+                        dc_dev_out ? dc_dev_out : h->dc_work, h->partials);
+    reduce_to(c, h->partials, h->dtmp);
+    if (C_out) {
+        CK(h, cudaMemcpyAsync(C_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* out_dev, int transpose) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!in_dev || !out_dev || in_dev == out_dev) return fail(h, TOPO_BADARG, "bad pointers");
+    s = prepare_filter(h, r);
+    if (s != TOPO_OK) return s;
+    filter_launch(h->ctx(), h->lev[0].g, h->offs, h->wts, h->noffs, in_dev, out_dev, transpose ? 1 : 0, h->S_cache);
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac, double* rho_dev_inout,
+                           const double* dc_dev, double* change_out) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev_inout || !dc_dev) return fail(h, TOPO_BADARG, "NULL pointer");
+    if (!(move > 0.0 && move <= 1.0) || !(volfrac > 0.0 && volfrac < 1.0))
+        return fail(h, TOPO_BADARG, "move must be in (0,1], volfrac in (0,1)");
+    s = prepare_filter(h, r);
+    if (s != TOPO_OK) return s;
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    filter_launch(c, g, h->offs, h->wts, h->noffs, dc_dev, h->dc_work, 1, h->S_cache);
+    oc_prepare(c, g.ne, h->dc_work, h->dc_work);
+    const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
+    const double init[8] = {l1, l2, 0.5 * (l1 + l2), (l2 - l1) / (l1 + l2) > tol ? 0.0 : 1.0, 0.0, 0.5 * (l1 + l2),
+                            0.0, 0.0};
+    CK(h, cudaMemcpyAsync(h->lam, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    double state[8];
+    for (int batch = 0; batch < 25; ++batch) {
+        for (int k = 0; k < 16; ++k) {
+            oc_bisect_step(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->partials, h->lam);
+            oc_bisect_finalize(c, h->partials, h->lam, volfrac * (double)g.ne, tol);
+        }
+        CK(h, cudaMemcpyAsync(state, h->lam, sizeof(state), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (state[3] != 0.0) break;
+    }
+    if (state[3] == 0.0) return fail(h, TOPO_MAXITER, "bisection did not converge");
+    oc_write(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->lam, h->partials, h->dtmp);
+    if (change_out) {
+        CK(h, cudaMemcpyAsync(change_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_level_dims(topo_handle h, int level, int* nx, int* ny, int* nz) {
+    if (!h || level < 0 || level >= h->L || !nx || !ny || !nz) return TOPO_BADARG;
+    *nx = h->lev[level].g.nx;
+    *ny = h->lev[level].g.ny;
+    *nz = h->lev[level].g.nz;
+    return TOPO_OK;
+}
+
+static topo_status step_check(topo_grid* h, int level, int precision) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (level < 0 || level >= h->L) return fail(h, TOPO_BADARG, "level out of range");
+    if (precision != TOPO_FP64 && precision != TOPO_MIXED) return fail(h, TOPO_BADARG, "precision must be 0 or 1");
+    if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
+    return alloc_precision(h, precision == TOPO_FP64);
+}
+
+// runs a level operator in FP32: inputs rounded into level buffers, result widened
+enum { OP_APPLY, OP_JACOBI, OP_RESID };
+static topo_status level_op(topo_grid* h, int level, int precision, int op, const double* u, const double* f,
+                            double* out) {
+    topo_status s = step_check(h, level, precision);
+    if (s != TOPO_OK) return s;
+    if (!u || !out || (op != OP_APPLY && !f)) return fail(h, TOPO_BADARG, "NULL pointer");
+    const int mode = op == OP_APPLY ? ST_APPLY : (op == OP_JACOBI ? ST_JACOBI : ST_RESID);
+    const Ctx c = h->ctx();
+    Level& lv = h->lev[level];
+    const long long n = 3 * lv.g.nn;
+    if (precision == TOPO_FP64) {
+        op_apply<double>(h, mode, level, u, f, out, nullptr);
+    } else {
+        convert<double, float>(c, n, u, lv.v32.a);
+        if (f) convert<double, float>(c, n, f, lv.v32.f);
+        op_apply<float>(h, mode, level, lv.v32.a, f ? lv.v32.f : nullptr, lv.v32.b, nullptr);
+        convert<float, double>(c, n, lv.v32.b, out);
+    }
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_apply_operator(topo_handle h, int level, int precision, const double* u_dev, double* y_dev) {
+    return level_op(h, level, precision, OP_APPLY, u_dev, nullptr, y_dev);
+}
+topo_status topo_jacobi_sweep(topo_handle h, int level, int precision, const double* u_dev, const double* f_dev,
+                              double* u_out_dev) {
+    return level_op(h, level, precision, OP_JACOBI, u_dev, f_dev, u_out_dev);
+}
+topo_status topo_residual(topo_handle h, int level, int precision, const double* u_dev, const double* f_dev,
+                          double* r_dev) {
+    return level_op(h, level, precision, OP_RESID, u_dev, f_dev, r_dev);
+}
+
+topo_status topo_restrict(topo_handle h, int level, const double* fine_dev, double* coarse_dev) {
+    topo_status s = step_check(h, level, TOPO_FP64);
+    if (s != TOPO_OK) return s;
+    if (level + 1 >= h->L || !fine_dev || !coarse_dev) return fail(h, TOPO_BADARG, "bad level or pointer");
+    restrict_residual<double>(h->ctx(), h->lev[level].g, h->lev[level].mask, h->lev[level + 1].mask, fine_dev,
+                              coarse_dev);
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_prolong_add(topo_handle h, int level, const double* coarse_dev, double* fine_dev) {
+    topo_status s = step_check(h, level, TOPO_FP64);
+    if (s != TOPO_OK) return s;
+    if (level + 1 >= h->L || !fine_dev || !coarse_dev) return fail(h, TOPO_BADARG, "bad level or pointer");
+    prolong_add<double>(h->ctx(), h->lev[level].g, h->lev[level].mask, h->lev[level + 1].mask, coarse_dev, fine_dev);
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_level_density(topo_handle h, int level, double* rho_dev_out) {
+    topo_status s = step_check(h, level, TOPO_FP64);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev_out) return fail(h, TOPO_BADARG, "NULL pointer");
+    CK(h, cudaMemcpyAsync(rho_dev_out, h->lev[level].rho, sizeof(double) * h->lev[level].g.ne,
+                          cudaMemcpyDeviceToDevice, h->stream));
+    return TOPO_OK;
+}
+
+topo_status topo_vcycle(topo_handle h, int precision, const double* r_dev, double* z_dev) {
+    topo_status s = step_check(h, 0, precision);
+    if (s != TOPO_OK) return s;
+    if (!r_dev || !z_dev || r_dev == z_dev) return fail(h, TOPO_BADARG, "bad pointers");
+    s = ensure_coarse(h);
+    if (s != TOPO_OK) return s;
+    Level& l0 = h->lev[0];
+    const long long n = 3 * l0.g.nn;
+    if (precision == TOPO_FP64) {
+        vcycle<double>(h, 0, r_dev, z_dev, l0.v64.a, nullptr);
+    } else {
+        const Ctx c = h->ctx();
+        convert<double, float>(c, n, r_dev, l0.v32.f);
+        vcycle<float>(h, 0, l0.v32.f, l0.v32.b, l0.v32.a, nullptr);
+        convert<float, double>(c, n, l0.v32.b, z_dev);
+    }
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_get_stats(topo_handle h, topo_solve_stats* out) {
+    if (!h || !out) return TOPO_BADARG;
+    *out = h->stats;
+    return TOPO_OK;
+}
+
+topo_status topo_launch_count(topo_handle h, long long* out) {
+    if (!h || !out) return TOPO_BADARG;
+    *out = h->launches;
+    return TOPO_OK;
+}
+
+topo_status topo_reset_solution(topo_handle h) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * 3 * h->lev[0].g.nn, h->stream));
+    return TOPO_OK;
+}
+
+topo_status topo_profile_enable(topo_handle h, int on) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->prof_on = on != 0;
+    if (on) {
+        h->prof_n = 0;
+        h->prof_kind.clear();
+    }
+    return TOPO_OK;
+}
+
+topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (mode < 0 || mode > 3 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
+    CK(h, cudaStreamSynchronize(h->stream));
+    launches[0] = launches[1] = 0;
+    total_ms[0] = total_ms[1] = 0.0;
+    for (int i = 0; i < h->prof_n; ++i) {
+        const int k = h->prof_kind[i];
+        if (k / 2 != mode) continue;
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+        launches[k & 1] += 1;
+        total_ms[k & 1] += ms;
+    }
+    return TOPO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations of the GB300 topology-optimisation library.
+// Layout in HBM (all device arrays, natural x-fastest indexing):
+//   nodal vectors  : interleaved 3*nn scalars, dof = 3*n + c
+//   element arrays : ne scalars, e = i + nx*(j + ny*k)
+//   Dirichlet mask : one byte per node, bit c set = DOF c fixed
+//   per level      : modulus E_l (FP64 and FP32 copies) with the element
+//                    scale 2^l folded in, homogenized density, mask, and the
+//                    V-cycle work vectors of each precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "modal.cuh"
+#include "topo.h"
+
+namespace topo {
+
+struct Ctx {
+    cudaStream_t s;
+    long long* launches;
+};
+
+struct Geom {
+    int nx, ny, nz;       // elements per axis
+    long long nn, ne;     // nodes, elements
+    int NX() const { return nx + 1; }
+    int NY() const { return ny + 1; }
+    int NZ() const { return nz + 1; }
+};
+
+template <typename T>
+struct VBuf {             // V-cycle work vectors of one level in one precision
+    T* a = nullptr;
+    T* b = nullptr;
+    T* f = nullptr;       // right-hand side (levels > 0)
+};
+
+struct Level {
+    Geom g;
+    double scale = 1.0;       // 2^l
+    double* rho = nullptr;    // homogenized density
+    double* E64 = nullptr;    // 2^l * (Emin + rho^p (E0 - Emin))
+    float* E32 = nullptr;
+    uint8_t* mask = nullptr;
+    VBuf<double> v64;
+    VBuf<float> v32;
+};
+
+struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
+    int n = 0, npad = 0;
+    double* A = nullptr;      // npad^2 work matrix (assembly, Cholesky factor)
+    double* W64 = nullptr;    // L^-1 (lower, row-major npad^2)
+    double* WT64 = nullptr;   // (L^-1)^T (upper, row-major)
+    float* W32 = nullptr;
+    float* WT32 = nullptr;
+    double* y64 = nullptr;    // temporaries of length npad
+    float* y32 = nullptr;
+    int* info = nullptr;      // device: first non-positive pivot + 1 (0 = ok)
+};
+
+struct Scalars {              // device-resident CG scalars
+    double rz, rz_new, pq, rr, alpha, beta, ff, aux;
+};
+
+}  // namespace topo
+
+struct topo_grid {
+    topo_params prm{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int L = 1;
+    std::vector<topo::Level> lev;
+    topo::Coarse cs;
+    // fine-level vectors (interleaved, 3*nn)
+    double *x = nullptr, *f = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+    double* K0d = nullptr;          // reference element matrix (E = 1, h = 1), 24x24
+    float* K0f = nullptr;
+    topo::ModalCoef modal{};
+    double* dc_work = nullptr;      // element work arrays (filter / OC)
+    double* dv_work = nullptr;
+    double* xnew_work = nullptr;
+    double* S_cache = nullptr;      // filter weight sums S_e for S_radius
+    double* dv_cache = nullptr;     // H^T 1 for S_radius
+    int4* offs = nullptr;           // filter offsets for S_radius
+    double* wts = nullptr;          // filter weights for S_radius
+    int noffs = 0;
+    double S_radius = -1.0;
+    double* lam = nullptr;          // OC bisection state (device)
+    double* dtmp = nullptr;         // device scratch scalars
+    int* dflag = nullptr;           // device: density out of [0,1] seen
+    bool coarse_dirty = true;
+    // launch timing of fine-level operator kernels (topo_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;     // 2 per record
+    std::vector<int> prof_kind;           // mode * 2 + (float ? 1 : 0)
+    int prof_n = 0;
+    double* partials = nullptr;     // reduction partials
+    topo::Scalars* sc = nullptr;    // device scalars
+    double* host_sc = nullptr;      // pinned host mirror
+    bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false;
+    long long launches = 0;
+    topo_solve_stats stats{};
+    std::string err;
+    topo::Ctx ctx() { return topo::Ctx{stream, &launches}; }
+};
+
+namespace topo {
+
+constexpr int kRedBlocks = 1024;   // fixed grid of reduction kernels (deterministic order)
+constexpr int kProfMax = 65536;    // launch records of topo_profile_enable
+
+// ---- stencil.cu ----------------------------------------------------------
+enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3 };
+// out = op(u, f); with dot != nullptr also writes per-block partial sums of
+//   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
+template <typename T>
+void stencil(const Ctx& c, int mode, const Geom& g, const T* K0, const T* E, const uint8_t* mask, const T* u,
+             const T* f, T* out, T omega, double* dot_partials);
+void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
+                     double* A, int npad);
+void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
+                         double E0, double Emin, double penal, double* dc_out, double* partials);
+
+// ---- transfer.cu ---------------------------------------------------------
+template <typename T>
+void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc,
+                       const T* rf, T* rc);
+template <typename T>
+void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc,
+                 const T* ec, T* uf);
+void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c);
+void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0,
+                 double Emin, double penal, double* E64, float* E32, int* bad_flag);
+void mask_from_dofs(const Ctx& c, long long nn, const uint8_t* fixed_dofs, uint8_t* mask);
+void inject_mask(const Ctx& c, const Geom& gf, const uint8_t* maskf, uint8_t* maskc);
+void masked_copy_load(const Ctx& c, long long nn, const uint8_t* mask, const double* fin, double* fout);
+
+// ---- blas.cu -------------------------------------------------------------
+template <typename A, typename B>
+void dot_partials(const Ctx& c, long long n, const A* a, const B* b, double* partials);
+// reduces kRedBlocks partials into *dst (device double)
+void reduce_to(const Ctx& c, const double* partials, double* dst);
+// CG scalar steps, all on device: alpha = rz/pq ; beta = rz_new/rz, rz = rz_new
+void cg_alpha(const Ctx& c, const double* partials, Scalars* sc);
+void cg_beta(const Ctx& c, const double* partials, Scalars* sc);
+template <typename T>
+void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, const T* q, T* x, T* r,
+                  double* partials);
+template <typename T>
+void cg_update_p(const Ctx& c, long long n, const Scalars* sc, const T* z, T* p);
+template <typename S, typename D>
+void convert(const Ctx& c, long long n, const S* src, D* dst);
+void axpy_f32_into_f64(const Ctx& c, long long n, const float* d, double* x);
+template <typename T>
+void zero(const Ctx& c, long long n, T* v);
+void fill(const Ctx& c, long long n, double* v, double value);
+// dense coarse solve
+void chol_factor(const Ctx& c, double* A, int npad, int* info);
+void tri_inverse(const Ctx& c, const double* L, double* W, int npad);
+void transpose_dense(const Ctx& c, const double* W, double* WT, int npad);
+template <typename T>
+void coarse_apply(const Ctx& c, int n, int npad, const T* W, const T* WT, const T* rhs, T* y, T* out);
+
+// ---- filter_oc.cu --------------------------------------------------------
+// mode 0: filter, 1: transpose (needs S), 2: write the weight sums S
+void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs, const double* in,
+                   double* out, int mode, const double* S);
+void oc_prepare(const Ctx& c, long long ne, const double* dct, double* num);
+void oc_bisect_step(const Ctx& c, long long ne, const double* x, const double* num, const double* dv,
+                    double move, double* partials, double* lam_state);
+void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state, double volfrac_ne,
+                        double tol);
+void oc_write(const Ctx& c, long long ne, double* x, const double* num, const double* dv, double move,
+              const double* lam_state, double* partials, double* change_dst);
+
+}  // namespace topo
+
+#define TOPO_LAUNCH_CHECK(ctx)                 \
+    do {                                       \
+        ++*(ctx).launches;                     \
+    } while (0)

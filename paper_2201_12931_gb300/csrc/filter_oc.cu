@@ -1,0 +1,195 @@
+// Density filter (weights of Eqs. Neighbourhood / NB_dist, normalised by the
+// in-domain weight sum), its transpose, and the optimality-criteria update with
+// bisection on the Lagrange multiplier (Eqs. OCUp1, bisect).
+//
+// The volume of the filtered new design is evaluated without filtering it:
+// mean(H x) = (1/N) sum_e sum_i w_ei x_i / S_e = (1/N) (H^T 1)^T x, so one
+// bisection step is a single pass over (x, -dc~, H^T 1) with an FP64 block sum.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace topo {
+
+namespace {
+
+inline unsigned grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    }
+    return t;
+}
+
+// mode 0: out_e = sum_d w_d in[e+d] / S_e (S_e on the fly)
+// mode 1: out_i = sum_d w_d in[i+d] / S[i+d]
+// mode 2: out_e = S_e
+template <int MODE>
+__global__ void __launch_bounds__(256) k_filter(const int4* __restrict__ offs, const double* __restrict__ wts,
+                                                int noffs, int nx, int ny, int nz, const double* __restrict__ in,
+                                                const double* __restrict__ S, double* __restrict__ out) {
+    extern __shared__ int4 soff[];                       // offsets first: 16-byte aligned
+    double* sw = reinterpret_cast<double*>(soff + noffs);
+    for (int t = threadIdx.x; t < noffs; t += blockDim.x) {
+        sw[t] = wts[t];
+        soff[t] = offs[t];
+    }
+    __syncthreads();
+    const long long ne = (long long)nx * ny * nz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % nx);
+        const long long t = e / nx;
+        const int j = (int)(t % ny), k = (int)(t / ny);
+        double acc = 0.0, ws = 0.0;
+        for (int q = 0; q < noffs; ++q) {
+            const int4 o = soff[q];
+            const int a = i + o.x, b = j + o.y, c = k + o.z;
+            if (a < 0 || a >= nx || b < 0 || b >= ny || c < 0 || c >= nz) continue;
+            const double w = sw[q];
+            const long long nb = a + (long long)nx * (b + (long long)ny * c);
+            if (MODE == 0) {
+                acc += w * in[nb];
+                ws += w;
+            } else if (MODE == 1) {
+                acc += w * (in[nb] / S[nb]);
+            } else {
+                ws += w;
+            }
+        }
+        out[e] = (MODE == 0) ? acc / ws : (MODE == 1 ? acc : ws);
+    }
+}
+
+__global__ void k_oc_prepare(long long ne, const double* __restrict__ dct, double* __restrict__ num) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    num[e] = fmax(-dct[e], 1e-30);
+}
+
+// lam state: [0] l1, [1] l2, [2] lmid (next to evaluate), [3] done, [4] steps, [5] last lmid
+__device__ __forceinline__ double oc_candidate(double x, double num, double dv, double lam, double move) {
+    const double cand = x * sqrt(num / (lam * dv));
+    return fmax(0.0, fmax(x - move, fmin(1.0, fmin(x + move, cand))));
+}
+
+__global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __restrict__ x, const double* __restrict__ num,
+                                                 const double* __restrict__ dv, double move, double* __restrict__ partials,
+                                                 const double* __restrict__ lam) {
+    __shared__ double sh[32];
+    if (lam[3] != 0.0) {
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        return;
+    }
+    const double lm = lam[2];
+    double s = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
+        s += dv[e] * oc_candidate(x[e], num[e], dv[e], lm, move);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_oc_finalize(const double* __restrict__ partials, double* lam, double volfrac_ne,
+                                                      double tol) {
+    __shared__ double sh[32];
+    if (lam[3] != 0.0) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) s += partials[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double lm = lam[2];
+        if (s > volfrac_ne) lam[0] = lm;
+        else lam[1] = lm;
+        lam[5] = lm;
+        lam[4] += 1.0;
+        const double l1 = lam[0], l2 = lam[1];
+        if ((l2 - l1) / (l1 + l2) > tol) lam[2] = 0.5 * (l1 + l2);
+        else lam[3] = 1.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_oc_write(long long ne, double* __restrict__ x, const double* __restrict__ num,
+                                                  const double* __restrict__ dv, double move, const double* __restrict__ lam,
+                                                  double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const double lm = lam[5];
+    double m = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+        const double xo = x[e];
+        const double xn = oc_candidate(xo, num[e], dv[e], lm, move);
+        m = fmax(m, fabs(xn - xo));
+        x[e] = xn;
+    }
+    m = block_max(m, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = m;
+}
+
+__global__ void __launch_bounds__(1024) k_max_to(const double* __restrict__ partials, double* dst) {
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) m = fmax(m, partials[i]);
+    m = block_max(m, sh);
+    if (threadIdx.x == 0) *dst = m;
+}
+
+}  // namespace
+
+void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs, const double* in,
+                   double* out, int mode, const double* S) {
+    unsigned blocks = grid_for(g.ne, 256);
+    if (blocks > 16384) blocks = 16384;
+    const size_t sm = (sizeof(int4) + sizeof(double)) * (size_t)noffs;
+    if (mode == 0) k_filter<0><<<blocks, 256, sm, c.s>>>(offs, wts, noffs, g.nx, g.ny, g.nz, in, S, out);
+    else if (mode == 1) k_filter<1><<<blocks, 256, sm, c.s>>>(offs, wts, noffs, g.nx, g.ny, g.nz, in, S, out);
+    else k_filter<2><<<blocks, 256, sm, c.s>>>(offs, wts, noffs, g.nx, g.ny, g.nz, in, S, out);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_prepare(const Ctx& c, long long ne, const double* dct, double* num) {
+    k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, dct, num);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_bisect_step(const Ctx& c, long long ne, const double* x, const double* num, const double* dv, double move,
+                    double* partials, double* lam_state) {
+    k_oc_step<<<kRedBlocks, 256, 0, c.s>>>(ne, x, num, dv, move, partials, lam_state);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state, double volfrac_ne, double tol) {
+    k_oc_finalize<<<1, 1024, 0, c.s>>>(partials, lam_state, volfrac_ne, tol);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_write(const Ctx& c, long long ne, double* x, const double* num, const double* dv, double move,
+              const double* lam_state, double* partials, double* change_dst) {
+    k_oc_write<<<kRedBlocks, 256, 0, c.s>>>(ne, x, num, dv, move, lam_state, partials);
+    TOPO_LAUNCH_CHECK(c);
+    k_max_to<<<1, 1024, 0, c.s>>>(partials, change_dst);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+}  // namespace topo

@@ -1,0 +1,227 @@
+// Host orchestration of the state solve, all work enqueued on the handle's
+// stream:
+//   * V-cycle (Algorithm 3) with damped-Jacobi smoothing, residual
+//     restriction, recursion from a zero iterate, prolongation correction and
+//     the direct solve on the coarsest grid;
+//   * preconditioned CG (Algorithm 1, standard initialisation r0 = f - K x0,
+//     z0 = M^-1 r0, p0 = z0), scalars kept on the device;
+//   * FP64 iterative refinement around an FP32 inner MGPCG (mixed modes):
+//     r = f - K x in FP64, solve K d ~= r in FP32, x += d, repeat.
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+#include "solver.h"
+
+namespace topo {
+
+template <typename T>
+struct P;
+template <>
+struct P<double> {
+    static const double* K0(topo_grid* h) { return h->K0d; }
+    static const double* E(Level& l) { return l.E64; }
+    static VBuf<double>& vb(Level& l) { return l.v64; }
+    static const double* W(topo_grid* h) { return h->cs.W64; }
+    static const double* WT(topo_grid* h) { return h->cs.WT64; }
+    static double* y(topo_grid* h) { return h->cs.y64; }
+};
+template <>
+struct P<float> {
+    static const float* K0(topo_grid* h) { return h->K0f; }
+    static const float* E(Level& l) { return l.E32; }
+    static VBuf<float>& vb(Level& l) { return l.v32; }
+    static const float* W(topo_grid* h) { return h->cs.W32; }
+    static const float* WT(topo_grid* h) { return h->cs.WT32; }
+    static float* y(topo_grid* h) { return h->cs.y32; }
+};
+
+template <typename T>
+void op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot) {
+    Level& lv = h->lev[l];
+    const bool rec = h->prof_on && l == 0 && h->prof_n < kProfMax;
+    if (rec) {
+        if ((int)h->prof_ev.size() < 2 * (h->prof_n + 1)) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            h->prof_ev.push_back(a);
+            h->prof_ev.push_back(b);
+        }
+        cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
+    }
+    stencil<T>(h->ctx(), mode, lv.g, P<T>::K0(h), P<T>::E(lv), lv.mask, u, f, out, (T)h->prm.omega, dot);
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
+        h->prof_kind.resize(h->prof_n + 1);
+        h->prof_kind[h->prof_n] = mode * 2 + (sizeof(T) == 4 ? 1 : 0);
+        ++h->prof_n;
+    }
+}
+template void op_apply<double>(topo_grid*, int, int, const double*, const double*, double*, double*);
+template void op_apply<float>(topo_grid*, int, int, const float*, const float*, float*, double*);
+
+template <typename T>
+void vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
+    const Ctx c = h->ctx();
+    Level& lv = h->lev[l];
+    if (l == h->L - 1) {
+        coarse_apply<T>(c, h->cs.n, h->cs.npad, P<T>::W(h), P<T>::WT(h), f, P<T>::y(h), out);
+        if (dot) dot_partials<T, T>(c, 3 * lv.g.nn, f, out, dot);
+        return;
+    }
+    const int pre = h->prm.pre, post = h->prm.post;
+    const int nflip = (pre > 0 ? pre - 1 : 0) + post;
+    T* cur = (nflip & 1) ? tmp : out;
+    T* oth = (cur == out) ? tmp : out;
+    const long long n = 3 * lv.g.nn;
+    if (pre > 0) {
+        op_apply<T>(h, ST_JACOBI0, l, nullptr, f, cur, nullptr);
+        for (int s = 1; s < pre; ++s) {
+            op_apply<T>(h, ST_JACOBI, l, cur, f, oth, nullptr);
+            T* t = cur; cur = oth; oth = t;
+        }
+        op_apply<T>(h, ST_RESID, l, cur, f, oth, nullptr);
+    } else {
+        zero<T>(c, n, cur);
+        cudaMemcpyAsync(oth, f, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    Level& lc = h->lev[l + 1];
+    VBuf<T>& vc = P<T>::vb(lc);
+    restrict_residual<T>(c, lv.g, lv.mask, lc.mask, oth, vc.f);
+    vcycle<T>(h, l + 1, vc.f, vc.a, vc.b, nullptr);
+    prolong_add<T>(c, lv.g, lv.mask, lc.mask, vc.a, cur);
+    for (int s = 0; s < post; ++s) {
+        op_apply<T>(h, ST_JACOBI, l, cur, f, oth, (s == post - 1) ? dot : nullptr);
+        T* t = cur; cur = oth; oth = t;
+    }
+    if (post == 0 && dot) dot_partials<T, T>(c, n, f, cur, dot);
+}
+template void vcycle<double>(topo_grid*, int, const double*, double*, double*, double*);
+template void vcycle<float>(topo_grid*, int, const float*, float*, float*, double*);
+
+// copies the scalars to the pinned mirror and waits for them
+static void fetch_scalars(topo_grid* h) {
+    cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+}
+
+// PCG on level 0 in precision T.  r holds the right-hand side residual on
+// entry (r = b - K x already formed, ||r||^2 in *rr0) and is updated in place.
+// Returns the number of iterations; *status gets OK / MAXITER / BREAKDOWN.
+template <typename T>
+static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, double target_rr, int max_it,
+                    int* status, double* rr_out) {
+    const Ctx c = h->ctx();
+    Level& l0 = h->lev[0];
+    const long long n = 3 * l0.g.nn;
+    VBuf<T>& vb = P<T>::vb(l0);
+    double rr = rr0;
+    *status = TOPO_OK;
+    if (rr <= target_rr) {
+        *rr_out = rr;
+        return 0;
+    }
+    cudaMemsetAsync(&h->sc->aux, 0, sizeof(double), h->stream);
+    vcycle<T>(h, 0, r, z, vb.a, h->partials);
+    cg_beta(c, h->partials, h->sc);   // sets rz (beta unused on the first step)
+    cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
+    int it = 0;
+    while (it < max_it) {
+        op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
+        cg_alpha(c, h->partials, h->sc);
+        cg_update_xr<T>(c, n, h->sc, p, q, x, r, h->partials);
+        reduce_to(c, h->partials, &h->sc->rr);
+        ++it;
+        fetch_scalars(h);
+        rr = h->host_sc[3];
+        if (h->host_sc[7] != 0.0 || !std::isfinite(rr)) {
+            *status = TOPO_BREAKDOWN;
+            break;
+        }
+        if (rr <= target_rr) break;
+        vcycle<T>(h, 0, r, z, vb.a, h->partials);
+        cg_beta(c, h->partials, h->sc);
+        cg_update_p<T>(c, n, h->sc, z, p);
+    }
+    if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;
+    *rr_out = rr;
+    return it;
+}
+
+static double residual64(topo_grid* h) {
+    op_apply<double>(h, ST_RESID, 0, h->x, h->f, h->r, h->partials);
+    reduce_to(h->ctx(), h->partials, &h->sc->rr);
+    fetch_scalars(h);
+    return h->host_sc[3];
+}
+
+int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres) {
+    const double ff = h->host_sc[6];
+    double rr_true = residual64(h);
+    int status = TOPO_OK, it = 0, restarts = 0;
+    // CG on the recursively updated residual; when it reports convergence the
+    // true residual f - K x is recomputed and, if the two have drifted apart,
+    // CG restarts from the true residual (at most 4 restarts)
+    for (;;) {
+        double rr;
+        it += pcg_core<double>(h, h->x, h->r, h->z, h->p, h->q, rr_true, tol * tol * ff, max_it - it, &status, &rr);
+        rr_true = residual64(h);
+        if (status != TOPO_OK || rr_true <= tol * tol * ff || restarts >= 4 || it >= max_it) break;
+        ++restarts;
+    }
+    *iters = it;
+    *relres = std::sqrt(rr_true / ff);
+    h->stats.outer_steps = restarts;
+    if (status == TOPO_OK && rr_true > tol * tol * ff) status = TOPO_MAXITER;
+    return status;
+}
+
+int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres) {
+    const Ctx c = h->ctx();
+    const long long n = 3 * h->lev[0].g.nn;
+    const double ff = h->host_sc[6];
+    double rr = residual64(h);
+    int total = 0, outer = 0, status = TOPO_OK;
+    double best = rr;
+    while (std::sqrt(rr / ff) > tol) {
+        if (outer >= h->prm.max_refine || total >= max_it) {
+            status = TOPO_MAXITER;
+            break;
+        }
+        convert<double, float>(c, n, h->r, h->r32);
+        zero<float>(c, n, h->d32);
+        dot_partials<float, float>(c, n, h->r32, h->r32, h->partials);
+        reduce_to(c, h->partials, &h->sc->rr);
+        fetch_scalars(h);
+        const double rr32 = h->host_sc[3];
+        int st;
+        double rr_in;
+        const double red = h->prm.inner_tol;
+        const double target = red * red * rr32;
+        const int it = pcg_core<float>(h, h->d32, h->r32, h->z32, h->p32, h->q32, rr32, target,
+                                       max_it - total, &st, &rr_in);
+        total += it;
+        axpy_f32_into_f64(c, n, h->d32, h->x);
+        ++outer;
+        const double rr_new = residual64(h);
+        if (st == TOPO_BREAKDOWN || !std::isfinite(rr_new)) {
+            status = TOPO_BREAKDOWN;
+            rr = rr_new;
+            break;
+        }
+        if (rr_new > 0.25 * best && std::sqrt(rr_new / ff) > tol) {   // refinement stagnates
+            rr = rr_new;
+            status = TOPO_MAXITER;
+            break;
+        }
+        best = std::fmin(best, rr_new);
+        rr = rr_new;
+    }
+    *iters = total;
+    *relres = std::sqrt(rr / ff);
+    h->stats.outer_steps = outer;
+    return status;
+}
+
+}  // namespace topo

@@ -1,0 +1,200 @@
+// Grid transfers and per-level set-up.
+//   restriction  r_c = diag(free_c) P^T diag(free_f) r_f  (Algorithm 3,
+//                "Restrict to next coarser grid"; trilinear P, 1D weights
+//                1 at coincident and 1/2 at midpoint nodes)
+//   prolongation u_f += diag(free_f) P diag(free_c) e_c  (Algorithm 3,
+//                "Prolongation correction")
+//   homogenization: coarse density = mean of the 8 children (Sec. 4.2.2)
+//   SIMP moduli E_l = 2^l (Emin + rho^p (E0 - Emin)) (Eq. K_mod)
+#include "common.cuh"
+
+namespace topo {
+
+namespace {
+
+inline unsigned grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__global__ void k_restrict(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
+                           const T* __restrict__ rf, T* __restrict__ rc, int nxf, int nyf, int nzf) {
+    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
+    const int NXc = nxc + 1, NYc = nyc + 1, NZc = nzc + 1;
+    const int NXf = nxf + 1, NYf = nyf + 1, NZf = nzf + 1;
+    const long long nnc = (long long)NXc * NYc * NZc;
+    const long long N = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (N >= nnc) return;
+    const int I = (int)(N % NXc);
+    const long long t = N / NXc;
+    const int J = (int)(t % NYc), K = (int)(t / NYc);
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int k = 2 * K + dz;
+        if (k < 0 || k >= NZf) continue;
+        const T wz = dz ? T(0.5) : T(1);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int j = 2 * J + dy;
+            if (j < 0 || j >= NYf) continue;
+            const T wy = dy ? T(0.5) : T(1);
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int i = 2 * I + dx;
+                if (i < 0 || i >= NXf) continue;
+                const T w = wz * wy * (dx ? T(0.5) : T(1));
+                const long long n = i + (long long)NXf * (j + (long long)NYf * k);
+                const unsigned mf = maskf[n];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (!((mf >> c) & 1u)) acc[c] += w * rf[3 * n + c];
+            }
+        }
+    }
+    const unsigned mc = maskc[N];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rc[3 * N + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
+}
+
+template <typename T>
+__global__ void k_prolong_add(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
+                              const T* __restrict__ ec, T* __restrict__ uf, int nxf, int nyf, int nzf) {
+    const int NXf = nxf + 1, NYf = nyf + 1, NZf = nzf + 1;
+    const int NXc = nxf / 2 + 1, NYc = nyf / 2 + 1;
+    const long long nnf = (long long)NXf * NYf * NZf;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nnf) return;
+    const int i = (int)(n % NXf);
+    const long long t = n / NXf;
+    const int j = (int)(t % NYf), k = (int)(t / NYf);
+    // per axis: one coarse node (even) or two with weight 1/2 (odd)
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int c2 = 0; c2 < nk; ++c2)
+        for (int b2 = 0; b2 < nj; ++b2)
+            for (int a2 = 0; a2 < ni; ++a2) {
+                const long long N = (I0 + a2) + (long long)NXc * ((J0 + b2) + (long long)NYc * (K0 + c2));
+                const unsigned mc = maskc[N];
+                const T w = wi * wj * wk;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (!((mc >> c) & 1u)) acc[c] += w * ec[3 * N + c];
+            }
+    const unsigned mf = maskf[n];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        if (!((mf >> c) & 1u)) uf[3 * n + c] += acc[c];
+}
+
+__global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__ rc, int nxf, int nyf,
+                             int nzf) {
+    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
+    const long long nec = (long long)nxc * nyc * nzc;
+    const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (E >= nec) return;
+    const int I = (int)(E % nxc);
+    const long long t = E / nxc;
+    const int J = (int)(t % nyc), K = (int)(t / nyc);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const long long e = (2 * I + (c & 1)) + (long long)nxf * ((2 * J + ((c >> 1) & 1)) + (long long)nyf * (2 * K + (c >> 2)));
+        s += rf[e];
+    }
+    rc[E] = 0.125 * s;
+}
+
+__global__ void k_simp(long long ne, const double* __restrict__ rho, double scale, double E0, double Emin,
+                       double penal, double* __restrict__ E64, float* __restrict__ E32, int* bad) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const double r = rho[e];
+    if (!(r >= 0.0 && r <= 1.0)) atomicExch(bad, 1);
+    const double rc = fmin(fmax(r, 0.0), 1.0);
+    const double E = scale * (Emin + pow(rc, penal) * (E0 - Emin));
+    E64[e] = E;
+    E32[e] = (float)E;
+}
+
+__global__ void k_mask_from_dofs(long long nn, const uint8_t* __restrict__ fixed, uint8_t* __restrict__ mask) {
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    mask[n] = (uint8_t)((fixed[3 * n] ? 1 : 0) | (fixed[3 * n + 1] ? 2 : 0) | (fixed[3 * n + 2] ? 4 : 0));
+}
+
+__global__ void k_inject_mask(const uint8_t* __restrict__ maskf, uint8_t* __restrict__ maskc, int nxf, int nyf,
+                              int nzf) {
+    const int NXc = nxf / 2 + 1, NYc = nyf / 2 + 1, NZc = nzf / 2 + 1;
+    const long long nnc = (long long)NXc * NYc * NZc;
+    const long long N = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (N >= nnc) return;
+    const int I = (int)(N % NXc);
+    const long long t = N / NXc;
+    const int J = (int)(t % NYc), K = (int)(t / NYc);
+    maskc[N] = maskf[2 * I + (long long)(nxf + 1) * (2 * J + (long long)(nyf + 1) * 2 * K)];
+}
+
+__global__ void k_masked_copy(long long nn, const uint8_t* __restrict__ mask, const double* __restrict__ fin,
+                              double* __restrict__ fout) {
+    const long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (d >= 3 * nn) return;
+    fout[d] = ((mask[d / 3] >> (d % 3)) & 1u) ? 0.0 : fin[d];
+}
+
+}  // namespace
+
+template <typename T>
+void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* rf,
+                       T* rc) {
+    const long long nnc = (long long)(gf.nx / 2 + 1) * (gf.ny / 2 + 1) * (gf.nz / 2 + 1);
+    k_restrict<T><<<grid_for(nnc, 256), 256, 0, c.s>>>(maskf, maskc, rf, rc, gf.nx, gf.ny, gf.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void restrict_residual<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
+                                        double*);
+template void restrict_residual<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*,
+                                       float*);
+
+template <typename T>
+void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* ec, T* uf) {
+    k_prolong_add<T><<<grid_for(gf.nn, 256), 256, 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void prolong_add<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
+                                  double*);
+template void prolong_add<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, float*);
+
+void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c) {
+    const long long nec = (long long)(gf.nx / 2) * (gf.ny / 2) * (gf.nz / 2);
+    k_homogenize<<<grid_for(nec, 256), 256, 0, c.s>>>(rho_f, rho_c, gf.nx, gf.ny, gf.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0, double Emin, double penal,
+                 double* E64, float* E32, int* bad_flag) {
+    k_simp<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, rho, scale, E0, Emin, penal, E64, E32, bad_flag);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void mask_from_dofs(const Ctx& c, long long nn, const uint8_t* fixed_dofs, uint8_t* mask) {
+    k_mask_from_dofs<<<grid_for(nn, 256), 256, 0, c.s>>>(nn, fixed_dofs, mask);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void inject_mask(const Ctx& c, const Geom& gf, const uint8_t* maskf, uint8_t* maskc) {
+    const long long nnc = (long long)(gf.nx / 2 + 1) * (gf.ny / 2 + 1) * (gf.nz / 2 + 1);
+    k_inject_mask<<<grid_for(nnc, 256), 256, 0, c.s>>>(maskf, maskc, gf.nx, gf.ny, gf.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void masked_copy_load(const Ctx& c, long long nn, const uint8_t* mask, const double* fin, double* fout) {
+    k_masked_copy<<<grid_for(3 * nn, 256), 256, 0, c.s>>>(nn, mask, fin, fout);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+}  // namespace topo

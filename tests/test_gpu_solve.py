@@ -1,0 +1,112 @@
+"""GPU state solve, compliance and sensitivity against the oracle.
+
+Bars: relative L2 displacement error and relative compliance error <= 1e-6
+at rel_tol 1e-8, and <= 1e-9 at rel_tol 1e-12 (FP64); sensitivity max error
+<= 1e-5 relative to max |dc|.  Mixed precision is held to the same bars
+(the FP64 refinement loop reaches the FP64 residual target).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import filter as oflt, state as ostate
+from gpu_common import cuda_device, n, t
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_solve(dims, levels, problem, rho, precision, tol):
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    import torch
+    pb = synth.cantilever(dims) if problem == "cantilever" else synth.mbb_half(dims)
+    g = TopoGrid(dims, Params(levels=levels, precision=precision))
+    g.set_density(t(rho))
+    g.set_bc_loads(t(pb.fixed), t(pb.f))
+    u = torch.empty(3 * g.nn, dtype=torch.float64, device=cuda_device())
+    _, res = g.solve(tol, 2000, out=u)
+    dc = torch.empty(g.ne, dtype=torch.float64, device=cuda_device())
+    C, _ = g.compliance_and_sensitivity(dc)
+    return g, pb, n(u), C, n(dc), res
+
+
+@pytest.mark.parametrize("dims,levels,problem", [
+    ((48, 24, 24), 3, "cantilever"),
+    ((32, 16, 16), 4, "mbb"),
+    ((12, 4, 4), 1, "cantilever"),
+])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_oracle(dims, levels, problem, precision):
+    rho = synth.uniform_field(dims, 1, 1e-3, 1.0)
+    rho = oflt.density_filter(rho, dims, 1.5)
+    pb = synth.cantilever(dims) if problem == "cantilever" else synth.mbb_half(dims)
+    u_o = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=1e-13)
+    C_o, _, dc_o = ostate.compliance_and_sensitivity(dims, rho, u_o, pb.f)
+    for tol, bar in ((1e-8, 1e-6), (1e-12, 1e-9)):
+        g, _, u, C, dc, res = _gpu_solve(dims, levels, problem, rho, precision, tol)
+        assert res.status == 0, res
+        assert res.relres <= tol
+        assert np.linalg.norm(u - u_o) <= bar * np.linalg.norm(u_o)
+        assert abs(C - C_o) <= bar * abs(C_o)
+        assert np.abs(dc - dc_o).max() <= max(bar, 1e-7) * np.abs(dc_o).max()
+        # energy identity C = f^T u on the GPU result
+        assert abs(C - pb.f @ u) <= 10 * tol * abs(C)
+
+
+def test_uniform_density_cantilever_48():
+    dims = (48, 24, 24)
+    rho = np.full(27648, 0.3)
+    pb = synth.cantilever(dims)
+    u_o = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=1e-13)
+    g, _, u, C, dc, res = _gpu_solve(dims, 3, "cantilever", rho, 0, 1e-8)
+    assert res.status == 0 and res.iters < 60
+    assert np.linalg.norm(u - u_o) <= 1e-6 * np.linalg.norm(u_o)
+
+
+def test_warm_start_reduces_iterations():
+    dims = (16, 8, 8)
+    rho = synth.uniform_field(dims, 2, 0.1, 1.0)
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    pb = synth.cantilever(dims)
+    g = TopoGrid(dims, Params(levels=3))
+    g.set_density(t(rho))
+    g.set_bc_loads(t(pb.fixed), t(pb.f))
+    _, r1 = g.solve(1e-8, 500)
+    _, r2 = g.solve(1e-8, 500)
+    assert r2.iters == 0 and r2.relres <= 1e-8
+
+
+def test_zero_load_gives_zero_solution():
+    dims = (8, 4, 4)
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    import torch
+    pb = synth.cantilever(dims)
+    g = TopoGrid(dims, Params(levels=2))
+    g.set_density(t(np.full(128, 0.5)))
+    g.set_bc_loads(t(pb.fixed), t(np.zeros_like(pb.f)))
+    u = torch.ones(3 * g.nn, dtype=torch.float64, device=cuda_device())
+    _, res = g.solve(1e-8, 100, out=u)
+    assert res.status == 0 and float(u.abs().max()) == 0.0
+
+
+def test_bad_density_is_rejected():
+    dims = (8, 4, 4)
+    from paper_2201_12931_gb300 import Params, TopoError, TopoGrid
+    pb = synth.cantilever(dims)
+    g = TopoGrid(dims, Params(levels=2))
+    rho = np.full(128, 0.5)
+    rho[7] = np.nan
+    g.set_density(t(rho))
+    g.set_bc_loads(t(pb.fixed), t(pb.f))
+    with pytest.raises(TopoError):
+        g.solve(1e-8, 100)
+
+
+def test_maxiter_reported():
+    dims = (16, 8, 8)
+    from paper_2201_12931_gb300 import Params, TopoGrid, TOPO_MAXITER
+    pb = synth.cantilever(dims)
+    g = TopoGrid(dims, Params(levels=2))
+    g.set_density(t(synth.uniform_field(dims, 3, 1e-3, 1.0)))
+    g.set_bc_loads(t(pb.fixed), t(pb.f))
+    _, res = g.solve(1e-14, 2)
+    assert res.status == TOPO_MAXITER and res.iters == 2
