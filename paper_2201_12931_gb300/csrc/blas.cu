@@ -50,21 +50,21 @@ __global__ void __launch_bounds__(256) k_dot(long long n, const A* __restrict__ 
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__device__ __forceinline__ double sum_partials(const double* __restrict__ p, double* sh) {
+__device__ __forceinline__ double sum_partials(const double* __restrict__ p, int n, double* sh) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < kRedBlocks; i += blockDim.x) s += p[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
     return block_sum(s, sh);
 }
 
-__global__ void __launch_bounds__(1024) k_reduce_to(const double* __restrict__ p, double* dst) {
+__global__ void __launch_bounds__(1024) k_reduce_to(const double* __restrict__ p, int n, double* dst) {
     __shared__ double sh[32];
-    const double s = sum_partials(p, sh);
+    const double s = sum_partials(p, n, sh);
     if (threadIdx.x == 0) *dst = s;
 }
 
-__global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p, Scalars* sc) {
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p, int n, Scalars* sc) {
     __shared__ double sh[32];
-    const double pq = sum_partials(p, sh);
+    const double pq = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         sc->pq = pq;
         if (pq > 0.0 && isfinite(pq) && isfinite(sc->rz)) {
@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p,
     }
 }
 
-__global__ void __launch_bounds__(1024) k_cg_beta(const double* __restrict__ p, Scalars* sc) {
+__global__ void __launch_bounds__(1024) k_cg_beta(const double* __restrict__ p, int n, Scalars* sc) {
     __shared__ double sh[32];
-    const double rz = sum_partials(p, sh);
+    const double rz = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         const double old = sc->rz;
         sc->rz_new = rz;
@@ -273,16 +273,16 @@ template void dot_partials<double, double>(const Ctx&, long long, const double*,
 template void dot_partials<float, float>(const Ctx&, long long, const float*, const float*, double*);
 template void dot_partials<double, float>(const Ctx&, long long, const double*, const float*, double*);
 
-void reduce_to(const Ctx& c, const double* partials, double* dst) {
-    k_reduce_to<<<1, 1024, 0, c.s>>>(partials, dst);
+void reduce_to(const Ctx& c, const double* partials, int n, double* dst) {
+    k_reduce_to<<<1, 1024, 0, c.s>>>(partials, n, dst);
     TOPO_LAUNCH_CHECK(c);
 }
-void cg_alpha(const Ctx& c, const double* partials, Scalars* sc) {
-    k_cg_alpha<<<1, 1024, 0, c.s>>>(partials, sc);
+void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc) {
+    k_cg_alpha<<<1, 1024, 0, c.s>>>(partials, n, sc);
     TOPO_LAUNCH_CHECK(c);
 }
-void cg_beta(const Ctx& c, const double* partials, Scalars* sc) {
-    k_cg_beta<<<1, 1024, 0, c.s>>>(partials, sc);
+void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc) {
+    k_cg_beta<<<1, 1024, 0, c.s>>>(partials, n, sc);
     TOPO_LAUNCH_CHECK(c);
 }
 

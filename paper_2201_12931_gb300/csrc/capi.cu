@@ -1,6 +1,7 @@
 // extern "C" entry points of include/topo.h: argument checks, device
 // workspace, per-level set-up (Sec. 4.2.2 homogenization), and dispatch to the
 // solver and the element / filter / OC kernels.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -9,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "operator.cuh"
 #include "solver.h"
 
 using namespace topo;
@@ -154,6 +156,10 @@ void free_all(topo_grid* h) {
     F(h->dc_work); F(h->dv_work); F(h->xnew_work); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
     F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
     if (h->host_sc) cudaFreeHost(h->host_sc);
+    delete h->mk64;
+    delete h->mk32;
+    h->mk64 = nullptr;
+    h->mk32 = nullptr;
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->prof_ev.clear();
 }
@@ -230,6 +236,43 @@ topo_status prepare_filter(topo_grid* h, double r) {
     return TOPO_OK;
 }
 
+// Operator coefficients of operator.cuh from the modal blocks; checks the
+// uniform block structure of the isotropic cube that the kernel relies on.
+bool build_modal_k(const ModalCoef& m, const double K0[576], ModalK<double>* k, std::string* err) {
+    double mx = 0.0;
+    for (int i = 0; i < 576; ++i) mx = std::fmax(mx, std::fabs(K0[i]));
+    const double tol = 1e-12 * mx;
+    bool ok = true;
+    auto same = [&](double a, double b) { ok = ok && std::fabs(a - b) <= tol; };
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            same(m.N[i][j], i == j ? m.N[0][0] : m.N[0][1]);
+            same(m.T3[i][j], i == j ? m.T3[0][0] : m.T3[0][1]);
+        }
+    for (int g = 0; g < 3; ++g)
+        for (int r = 0; r < 2; ++r)
+            for (int q = 0; q < 2; ++q) {
+                same(m.S[g][r][q], m.S[0][0][0]);
+                same(m.B[g][r][q], r == q ? m.B[0][0][0] : m.B[0][0][1]);
+            }
+    for (int r = 0; r < 3; ++r) same(m.C[r], m.C[0]);
+    for (int i = 0; i < 24; ++i) same(K0[i * 24 + i], K0[0]);
+    if (!ok) {
+        if (err) *err = "element matrix lacks the uniform modal block structure of the isotropic cube";
+        return false;
+    }
+    k->nd = m.N[0][0] - m.N[0][1];
+    k->no = m.N[0][1];
+    k->sc = m.S[0][0][0];
+    k->bp = m.B[0][0][0];
+    k->bq = m.B[0][0][1];
+    k->td = m.T3[0][0] - m.T3[0][1];
+    k->to = m.T3[0][1];
+    k->cg = m.C[0];
+    k->kdiag = K0[0];
+    return true;
+}
+
 topo_status check_handle(topo_grid* h) {
     if (!h) return TOPO_BADARG;
     h->err.clear();
@@ -297,11 +340,23 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     double K0[576];
     element_matrix(p.nu, K0);
     if (!build_modal(K0, &h->modal, &h->err)) return bail(TOPO_BADARG);
+    h->mk64 = new ModalK<double>();
+    h->mk32 = new ModalK<float>();
+    if (!build_modal_k(h->modal, K0, h->mk64, &h->err)) return bail(TOPO_BADARG);
+    {
+        const ModalK<double>& a = *h->mk64;
+        ModalK<float>& b = *h->mk32;
+        b.nd = (float)a.nd; b.no = (float)a.no; b.sc = (float)a.sc; b.bp = (float)a.bp; b.bq = (float)a.bq;
+        b.td = (float)a.td; b.to = (float)a.to; b.cg = (float)a.cg; b.kdiag = (float)a.kdiag;
+    }
     h->lev.resize(h->L);
+    h->npartials = kRedBlocks;
     for (int l = 0; l < h->L; ++l) {
         Level& lv = h->lev[l];
         lv.g = make_geom(nx >> l, ny >> l, nz >> l);
         lv.scale = (double)(1 << l);
+        lv.op = op_launch(lv.g);
+        h->npartials = std::max(h->npartials, lv.op.ctas());
     }
     topo_status st;
 #define TRY(expr)                          \
@@ -329,7 +384,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     TRY(dalloc(h, &h->lam, 8));
     TRY(dalloc(h, &h->dtmp, 8));
     TRY(dalloc(h, &h->dflag, 4));
-    TRY(dalloc(h, &h->partials, kRedBlocks));
+    TRY(dalloc(h, &h->partials, (size_t)h->npartials));
     TRY(dalloc(h, &h->sc, 1));
     h->cs.n = (int)std::min<long long>(3 * h->lev[h->L - 1].g.nn, 1LL << 30);
     h->cs.npad = (h->cs.n + 31) / 32 * 32;
@@ -399,7 +454,7 @@ topo_status topo_set_bc_loads(topo_handle h, const uint8_t* fixed_dev, const dou
     masked_copy_load(c, h->lev[0].g.nn, h->lev[0].mask, f_dev, h->f);
     CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * n0, h->stream));
     dot_partials<double, double>(c, n0, h->f, h->f, h->partials);
-    reduce_to(c, h->partials, &h->sc->ff);
+    reduce_to(c, h->partials, kRedBlocks, &h->sc->ff);
     CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->have_bc = true;
@@ -460,7 +515,7 @@ topo_status topo_compliance_and_sensitivity(topo_handle h, double* C_out, double
     const Geom& g = h->lev[0].g;
     element_energy_sens(c, g, h->modal, h->x, h->lev[0].rho, h->prm.E0, h->prm.Emin, h->prm.penal,
                         dc_dev_out ? dc_dev_out : h->dc_work, h->partials);
-    reduce_to(c, h->partials, h->dtmp);
+    reduce_to(c, h->partials, kRedBlocks, h->dtmp);
     if (C_out) {
         CK(h, cudaMemcpyAsync(C_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));

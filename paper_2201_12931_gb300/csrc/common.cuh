@@ -32,6 +32,15 @@ struct Geom {
     int NZ() const { return nz + 1; }
 };
 
+struct OpLaunch {          // launch geometry of the operator kernel on one level
+    Geom g;
+    int gx = 1, gy = 1, gz = 1, cz = 1;
+    long long ctas() const { return (long long)gx * gy * gz; }
+};
+
+template <typename T>
+struct ModalK;
+
 template <typename T>
 struct VBuf {             // V-cycle work vectors of one level in one precision
     T* a = nullptr;
@@ -41,6 +50,7 @@ struct VBuf {             // V-cycle work vectors of one level in one precision
 
 struct Level {
     Geom g;
+    OpLaunch op;
     double scale = 1.0;       // 2^l
     double* rho = nullptr;    // homogenized density
     double* E64 = nullptr;    // 2^l * (Emin + rho^p (E0 - Emin))
@@ -81,6 +91,9 @@ struct topo_grid {
     double* K0d = nullptr;          // reference element matrix (E = 1, h = 1), 24x24
     float* K0f = nullptr;
     topo::ModalCoef modal{};
+    topo::ModalK<double>* mk64 = nullptr;   // host copies of the operator coefficients
+    topo::ModalK<float>* mk32 = nullptr;
+    long long npartials = 0;                // size of the partials buffer
     double* dc_work = nullptr;      // element work arrays (filter / OC)
     double* dv_work = nullptr;
     double* xnew_work = nullptr;
@@ -116,11 +129,13 @@ constexpr int kProfMax = 65536;    // launch records of topo_profile_enable
 
 // ---- stencil.cu ----------------------------------------------------------
 enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3 };
-// out = op(u, f); with dot != nullptr also writes per-block partial sums of
+// out = op(u, f); with dot != nullptr also writes per-CTA partial sums of
 //   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
+// and returns the number of partials written.
+OpLaunch op_launch(const Geom& g);
 template <typename T>
-void stencil(const Ctx& c, int mode, const Geom& g, const T* K0, const T* E, const uint8_t* mask, const T* u,
-             const T* f, T* out, T omega, double* dot_partials);
+int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
+            const T* u, const T* f, T* out, T omega, double* dot_partials);
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
                      double* A, int npad);
 void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
@@ -143,11 +158,11 @@ void masked_copy_load(const Ctx& c, long long nn, const uint8_t* mask, const dou
 // ---- blas.cu -------------------------------------------------------------
 template <typename A, typename B>
 void dot_partials(const Ctx& c, long long n, const A* a, const B* b, double* partials);
-// reduces kRedBlocks partials into *dst (device double)
-void reduce_to(const Ctx& c, const double* partials, double* dst);
+// reduces n partials into *dst (device double), fixed order
+void reduce_to(const Ctx& c, const double* partials, int n, double* dst);
 // CG scalar steps, all on device: alpha = rz/pq ; beta = rz_new/rz, rz = rz_new
-void cg_alpha(const Ctx& c, const double* partials, Scalars* sc);
-void cg_beta(const Ctx& c, const double* partials, Scalars* sc);
+void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc);
+void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc);
 template <typename T>
 void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, const T* q, T* x, T* r,
                   double* partials);

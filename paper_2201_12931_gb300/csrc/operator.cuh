@@ -1,0 +1,126 @@
+// Element-by-element operator kernel (Sec. 4.2.1), GB300 form.
+//
+// Work decomposition.  A CTA of TX x TY threads owns an x-y tile of element
+// columns and marches along z through a chunk of node planes.  Thread (tx, ty)
+// owns the element column (i0-1+tx, j0-1+ty) and the node at its lower corner;
+// per layer it computes that column's element once, in the Walsh-Hadamard
+// (modal) basis of the brick (see modal.cuh):
+//     in-plane 2x2 transform of the new node plane (reused by the next layer)
+//     -> z butterfly -> 9-coefficient block stiffness scaled by E_e
+//     -> inverse z butterfly -> face accumulation with the layer below
+//     -> inverse in-plane transform = contributions to the 4 column corners.
+// Nodal values and corner contributions move between threads through
+// double-buffered shared memory with one __syncthreads per layer; each node
+// is read from HBM once per chunk (plus a one-node halo on the +x/+y sides
+// and one extra plane per chunk), and each output node is written once.
+// Outputs per CTA: (TX-1) x (TY-1) node columns.
+//
+// Operator with Dirichlet rows: y = P_f K P_f u + (I - P_f) u.  Epilogues:
+// K.u, damped Jacobi (Sec. 3.2) with the diagonal kdiag * sum_e E_e formed on
+// the fly, residual (Eq. residual), first Jacobi sweep from zero; each can
+// also emit per-CTA FP64 partial sums of a dot product.
+#pragma once
+
+#include "common.cuh"
+
+namespace topo {
+
+template <typename T>
+struct ModalK {           // structure verified on the host (build_modal_k)
+    T nd, no;             // normal-strain block: diagonal - off, off
+    T sc;                 // shear pairs: all four entries
+    T bp, bq;             // bilinear pairs: diagonal, off
+    T td, to;             // bilinear triple: diagonal - off, off
+    T cg;                 // trilinear diagonal
+    T kdiag;              // diagonal of K0 (the same for every DOF)
+};
+
+constexpr int kOpTX = 32;
+constexpr int kOpTY = 8;
+
+template <typename T>
+__device__ __forceinline__ void face_forward(const T* c00, const T* c10, const T* c01, const T* c11, T* F) {
+    // F[3*g + c], g = bx + 2 by
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T s0 = c10[c] + c00[c], d0 = c10[c] - c00[c];
+        const T s1 = c11[c] + c01[c], d1 = c11[c] - c01[c];
+        F[0 + c] = s1 + s0;
+        F[3 + c] = d1 + d0;
+        F[6 + c] = s1 - s0;
+        F[9 + c] = d1 - d0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void face_inverse(const T* A, T* c00, T* c10, T* c01, T* c11) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T lo0 = A[0 + c] - A[6 + c], hi0 = A[0 + c] + A[6 + c];   // bx = 0 : ay = 0 / 1
+        const T lo1 = A[3 + c] - A[9 + c], hi1 = A[3 + c] + A[9 + c];   // bx = 1
+        c00[c] = lo0 - lo1;
+        c10[c] = lo0 + lo1;
+        c01[c] = hi0 - hi1;
+        c11[c] = hi0 + hi1;
+    }
+}
+
+// element: bottom face modes FB, top face modes FT (12 each), modulus E ->
+// modal outputs folded back to face space: Bo (bottom), To (top)
+template <typename T>
+__device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* FB, const T* FT, T* Bo, T* To) {
+    T m[24];
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            m[3 * g + c] = FT[3 * g + c] + FB[3 * g + c];
+            m[3 * (g + 4) + c] = FT[3 * g + c] - FB[3 * g + c];
+        }
+    const T nd = E * k.nd, no = E * k.no, sc = E * k.sc, bp = E * k.bp, bq = E * k.bq;
+    const T td = E * k.td, to = E * k.to, cg = E * k.cg;
+    T w[24];
+    {   // normal strains {3, 7, 14}
+        const T s = no * (m[3] + m[7] + m[14]);
+        w[3] = nd * m[3] + s;
+        w[7] = nd * m[7] + s;
+        w[14] = nd * m[14] + s;
+    }
+    {   // shear pairs
+        w[4] = w[6] = sc * (m[4] + m[6]);
+        w[5] = w[12] = sc * (m[5] + m[12]);
+        w[8] = w[13] = sc * (m[8] + m[13]);
+    }
+    {   // bilinear pairs
+        w[9] = bp * m[9] + bq * m[20];
+        w[20] = bq * m[9] + bp * m[20];
+        w[10] = bp * m[10] + bq * m[17];
+        w[17] = bq * m[10] + bp * m[17];
+        w[15] = bp * m[15] + bq * m[19];
+        w[19] = bq * m[15] + bp * m[19];
+    }
+    {   // bilinear triple {11, 16, 18}
+        const T s = to * (m[11] + m[16] + m[18]);
+        w[11] = td * m[11] + s;
+        w[16] = td * m[16] + s;
+        w[18] = td * m[18] + s;
+    }
+    w[21] = cg * m[21];
+    w[22] = cg * m[22];
+    w[23] = cg * m[23];
+    // inverse z butterfly: bottom corner (az = 0) gets w_g - w_{g+4}; w_0..2 = 0
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Bo[c] = -w[12 + c];
+        To[c] = w[12 + c];
+    }
+#pragma unroll
+    for (int g = 1; g < 4; ++g)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Bo[3 * g + c] = w[3 * g + c] - w[3 * (g + 4) + c];
+            To[3 * g + c] = w[3 * g + c] + w[3 * (g + 4) + c];
+        }
+}
+
+}  // namespace topo

@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "operator.cuh"
 #include "solver.h"
 
 namespace topo {
@@ -19,7 +20,7 @@ template <typename T>
 struct P;
 template <>
 struct P<double> {
-    static const double* K0(topo_grid* h) { return h->K0d; }
+    static const ModalK<double>& mk(topo_grid* h) { return *h->mk64; }
     static const double* E(Level& l) { return l.E64; }
     static VBuf<double>& vb(Level& l) { return l.v64; }
     static const double* W(topo_grid* h) { return h->cs.W64; }
@@ -28,7 +29,7 @@ struct P<double> {
 };
 template <>
 struct P<float> {
-    static const float* K0(topo_grid* h) { return h->K0f; }
+    static const ModalK<float>& mk(topo_grid* h) { return *h->mk32; }
     static const float* E(Level& l) { return l.E32; }
     static VBuf<float>& vb(Level& l) { return l.v32; }
     static const float* W(topo_grid* h) { return h->cs.W32; }
@@ -37,7 +38,7 @@ struct P<float> {
 };
 
 template <typename T>
-void op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot) {
+int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot) {
     Level& lv = h->lev[l];
     const bool rec = h->prof_on && l == 0 && h->prof_n < kProfMax;
     if (rec) {
@@ -50,25 +51,27 @@ void op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, dou
         }
         cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
     }
-    stencil<T>(h->ctx(), mode, lv.g, P<T>::K0(h), P<T>::E(lv), lv.mask, u, f, out, (T)h->prm.omega, dot);
+    const int np = stencil<T>(h->ctx(), mode, lv.op, P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
+                              (T)h->prm.omega, dot);
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
         h->prof_kind.resize(h->prof_n + 1);
         h->prof_kind[h->prof_n] = mode * 2 + (sizeof(T) == 4 ? 1 : 0);
         ++h->prof_n;
     }
+    return dot ? np : 0;
 }
-template void op_apply<double>(topo_grid*, int, int, const double*, const double*, double*, double*);
-template void op_apply<float>(topo_grid*, int, int, const float*, const float*, float*, double*);
+template int op_apply<double>(topo_grid*, int, int, const double*, const double*, double*, double*);
+template int op_apply<float>(topo_grid*, int, int, const float*, const float*, float*, double*);
 
 template <typename T>
-void vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
+int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
     const Ctx c = h->ctx();
     Level& lv = h->lev[l];
     if (l == h->L - 1) {
         coarse_apply<T>(c, h->cs.n, h->cs.npad, P<T>::W(h), P<T>::WT(h), f, P<T>::y(h), out);
         if (dot) dot_partials<T, T>(c, 3 * lv.g.nn, f, out, dot);
-        return;
+        return dot ? kRedBlocks : 0;
     }
     const int pre = h->prm.pre, post = h->prm.post;
     const int nflip = (pre > 0 ? pre - 1 : 0) + post;
@@ -91,14 +94,19 @@ void vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
     restrict_residual<T>(c, lv.g, lv.mask, lc.mask, oth, vc.f);
     vcycle<T>(h, l + 1, vc.f, vc.a, vc.b, nullptr);
     prolong_add<T>(c, lv.g, lv.mask, lc.mask, vc.a, cur);
+    int np = 0;
     for (int s = 0; s < post; ++s) {
-        op_apply<T>(h, ST_JACOBI, l, cur, f, oth, (s == post - 1) ? dot : nullptr);
+        np = op_apply<T>(h, ST_JACOBI, l, cur, f, oth, (s == post - 1) ? dot : nullptr);
         T* t = cur; cur = oth; oth = t;
     }
-    if (post == 0 && dot) dot_partials<T, T>(c, n, f, cur, dot);
+    if (post == 0 && dot) {
+        dot_partials<T, T>(c, n, f, cur, dot);
+        np = kRedBlocks;
+    }
+    return dot ? np : 0;
 }
-template void vcycle<double>(topo_grid*, int, const double*, double*, double*, double*);
-template void vcycle<float>(topo_grid*, int, const float*, float*, float*, double*);
+template int vcycle<double>(topo_grid*, int, const double*, double*, double*, double*);
+template int vcycle<float>(topo_grid*, int, const float*, float*, float*, double*);
 
 // copies the scalars to the pinned mirror and waits for them
 static void fetch_scalars(topo_grid* h) {
@@ -123,15 +131,15 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
         return 0;
     }
     cudaMemsetAsync(&h->sc->aux, 0, sizeof(double), h->stream);
-    vcycle<T>(h, 0, r, z, vb.a, h->partials);
-    cg_beta(c, h->partials, h->sc);   // sets rz (beta unused on the first step)
+    int np = vcycle<T>(h, 0, r, z, vb.a, h->partials);
+    cg_beta(c, h->partials, np, h->sc);   // sets rz (beta unused on the first step)
     cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
     int it = 0;
     while (it < max_it) {
-        op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
-        cg_alpha(c, h->partials, h->sc);
+        np = op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
+        cg_alpha(c, h->partials, np, h->sc);
         cg_update_xr<T>(c, n, h->sc, p, q, x, r, h->partials);
-        reduce_to(c, h->partials, &h->sc->rr);
+        reduce_to(c, h->partials, kRedBlocks, &h->sc->rr);
         ++it;
         fetch_scalars(h);
         rr = h->host_sc[3];
@@ -140,8 +148,8 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
             break;
         }
         if (rr <= target_rr) break;
-        vcycle<T>(h, 0, r, z, vb.a, h->partials);
-        cg_beta(c, h->partials, h->sc);
+        np = vcycle<T>(h, 0, r, z, vb.a, h->partials);
+        cg_beta(c, h->partials, np, h->sc);
         cg_update_p<T>(c, n, h->sc, z, p);
     }
     if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;
@@ -150,8 +158,8 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
 }
 
 static double residual64(topo_grid* h) {
-    op_apply<double>(h, ST_RESID, 0, h->x, h->f, h->r, h->partials);
-    reduce_to(h->ctx(), h->partials, &h->sc->rr);
+    const int np = op_apply<double>(h, ST_RESID, 0, h->x, h->f, h->r, h->partials);
+    reduce_to(h->ctx(), h->partials, np, &h->sc->rr);
     fetch_scalars(h);
     return h->host_sc[3];
 }
@@ -192,7 +200,7 @@ int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres
         convert<double, float>(c, n, h->r, h->r32);
         zero<float>(c, n, h->d32);
         dot_partials<float, float>(c, n, h->r32, h->r32, h->partials);
-        reduce_to(c, h->partials, &h->sc->rr);
+        reduce_to(c, h->partials, kRedBlocks, &h->sc->rr);
         fetch_scalars(h);
         const double rr32 = h->host_sc[3];
         int st;

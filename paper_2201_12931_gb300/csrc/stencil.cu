@@ -8,6 +8,7 @@
 // fixed DOFs, K = sum_e E_e A_e^T K0 A_e (E_e already holds 2^l on level l).
 #include "common.cuh"
 #include "modal.cuh"
+#include "operator.cuh"
 
 namespace topo {
 
@@ -26,113 +27,238 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;   // valid in thread 0
 }
 
-// One thread per node; gathers the 8 adjacent elements' rows of E_e K0 u_e.
+// Element-column z-march operator kernel; see operator.cuh for the scheme.
 template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(256) k_stencil_gather(
-    const T* __restrict__ K0g, const T* __restrict__ E, const uint8_t* __restrict__ mask,
-    const T* __restrict__ u, const T* __restrict__ f, T* __restrict__ out, int nx, int ny, int nz,
-    T omega, double* __restrict__ partials) {
-    __shared__ T sK[576];
+__global__ void __launch_bounds__(kOpTX * kOpTY) k_op(ModalK<T> mk, const T* __restrict__ E,
+                                                      const uint8_t* __restrict__ mask, const T* __restrict__ u,
+                                                      const T* __restrict__ f, T* __restrict__ out, int nx, int ny,
+                                                      int nz, int cz, T omega, double* __restrict__ partials) {
+    constexpr int TX = kOpTX, TY = kOpTY;
+    constexpr bool NEEDU = (MODE != ST_JACOBI0);
+    constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
+    constexpr bool NEEDF = (MODE != ST_APPLY);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sU = reinterpret_cast<T*>(smem_raw);        // [2][TY+1][TX+1][3]   masked u of a node plane
+    T* sC = sU + 2 * (TY + 1) * (TX + 1) * 3;      // [2][3][TY][TX][3]     corner contributions 10, 01, 11
+    T* sE = sC + 2 * 3 * TY * TX * 3;              // [2][TY][TX]           column modulus sums
     __shared__ double sred[32];
-    for (int t = threadIdx.x; t < 576; t += blockDim.x) sK[t] = K0g[t];
-    __syncthreads();
-    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
-    const long long nn = (long long)NX * NY * NZ;
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int NX = nx + 1, NY = ny + 1;
+    const int i0 = blockIdx.x * (TX - 1), j0 = blockIdx.y * (TY - 1);
+    const int kz0 = blockIdx.z * cz;
+    const int kz1 = min(kz0 + cz, nz + 1);
+    const int in = i0 - 1 + tx, jn = j0 - 1 + ty;
+    const bool node_ok = in >= 0 && in < NX && jn >= 0 && jn < NY;
+    const bool col_ok = in >= 0 && in < nx && jn >= 0 && jn < ny;
+    const bool out_ok = tx >= 1 && ty >= 1 && node_ok;
+    // one halo node (+x column, +y row, +x+y corner) per thread with tid < TX + TY + 1
+    int hsx = TX, hsy = TY;
+    if (tid < TY + 1) { hsx = TX; hsy = tid; }
+    else if (tid < TY + 1 + TX) { hsx = tid - TY - 1; hsy = TY; }
+    const bool has_halo = tid < TY + 1 + TX;
+    const int hx = i0 - 1 + hsx, hy = j0 - 1 + hsy;
+    const bool halo_ok = has_halo && hx >= 0 && hx < NX && hy >= 0 && hy < NY;
+    const long long nplane = (long long)NX * NY;
+    const long long own_xy = node_ok ? (long long)in + (long long)NX * jn : 0;
+    const long long halo_xy = halo_ok ? (long long)hx + (long long)NX * hy : 0;
+    const long long col_xy = col_ok ? (long long)in + (long long)nx * jn : 0;
+    const long long eplane = (long long)nx * ny;
+
+    T fB[12], topPrev[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) fB[i] = topPrev[i] = T(0);
+    T st00[3] = {T(0), T(0), T(0)}, st10[3] = {T(0), T(0), T(0)}, st01[3] = {T(0), T(0), T(0)},
+      st11[3] = {T(0), T(0), T(0)};
+    T stE = T(0);
+    // own-node history (raw u, mask, f) of planes P-1 (h1) and P-2 (h2)
+    T h1u[3] = {T(0), T(0), T(0)}, h2u[3] = {T(0), T(0), T(0)};
+    T h1f[3] = {T(0), T(0), T(0)}, h2f[3] = {T(0), T(0), T(0)};
+    unsigned h1m = 0, h2m = 0;
+    T Elast = T(0);       // E of own column, layer P-2
     double dot = 0.0;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % NX);
-        const long long t2 = n / NX;
-        const int j = (int)(t2 % NY);
-        const int k = (int)(t2 / NY);
-        const unsigned mk = mask[n];
-        T acc[3] = {T(0), T(0), T(0)};
-        T dg[3] = {T(0), T(0), T(0)};
-#pragma unroll 1
-        for (int az = 0; az < 2; ++az) {
-            const int ez = k - 1 + az;
-            if (ez < 0 || ez >= nz) continue;
-#pragma unroll 1
-            for (int ay = 0; ay < 2; ++ay) {
-                const int ey = j - 1 + ay;
-                if (ey < 0 || ey >= ny) continue;
-#pragma unroll 1
-                for (int ax = 0; ax < 2; ++ax) {
-                    const int ex = i - 1 + ax;
-                    if (ex < 0 || ex >= nx) continue;
-                    const T Ee = E[ex + (long long)nx * (ey + (long long)ny * ez)];
-                    const int ln = (1 - ax) + 2 * (1 - ay) + 4 * (1 - az);
+
+    // prefetched data of plane P
+    T nu[3] = {T(0), T(0), T(0)}, nf[3] = {T(0), T(0), T(0)}, hu[3] = {T(0), T(0), T(0)};
+    unsigned nm = 0, hm = 0;
+    T nE = T(0);          // E of own column, layer P-1
+    auto fetch = [&](int P) {
+        const bool pin = P >= 0 && P <= nz;
+        const long long ob = (long long)P * nplane;
+        if (NEEDU || NEEDF) {
+            const bool ok = pin && node_ok;
+            nm = ok ? mask[ob + own_xy] : 0u;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) dg[c] += Ee * sK[(3 * ln + c) * 24 + 3 * ln + c];
-                    if (MODE != ST_JACOBI0) {
-                        T s[3] = {T(0), T(0), T(0)};
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            const long long nm = (ex + (m & 1)) +
-                                                 (long long)NX * ((ey + ((m >> 1) & 1)) + (long long)NY * (ez + (m >> 2)));
-                            const unsigned mm = mask[nm];
-                            const T v0 = (mm & 1u) ? T(0) : u[3 * nm + 0];
-                            const T v1 = (mm & 2u) ? T(0) : u[3 * nm + 1];
-                            const T v2 = (mm & 4u) ? T(0) : u[3 * nm + 2];
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                const T* row = &sK[(3 * ln + c) * 24 + 3 * m];
-                                s[c] += row[0] * v0 + row[1] * v1 + row[2] * v2;
-                            }
-                        }
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) acc[c] += Ee * s[c];
-                    }
-                }
+            for (int c = 0; c < 3; ++c) {
+                if (NEEDU) nu[c] = ok ? u[3 * (ob + own_xy) + c] : T(0);
+                if (NEEDF) nf[c] = ok ? f[3 * (ob + own_xy) + c] : T(0);
             }
         }
+        if (NEEDU) {
+            const bool okh = pin && halo_ok;
+            hm = okh ? mask[ob + halo_xy] : 0u;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hu[c] = okh ? u[3 * (ob + halo_xy) + c] : T(0);
+        }
+        const int L = P - 1;
+        nE = (col_ok && L >= 0 && L < nz) ? E[(long long)L * eplane + col_xy] : T(0);
+    };
+
+    fetch(kz0 - 1);
+    for (int P = kz0 - 1; P <= kz1 + 1; ++P) {
+        const int b = P & 1;
+        // current plane data
+        T cu[3], cf[3];
+        const unsigned cm = nm;
+        const T cE = nE;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const bool fixed = (mk >> c) & 1u;
-            const long long d = 3 * n + c;
-            T y;
-            if (MODE == ST_APPLY) {
-                const T uc = u[d];
-                y = fixed ? uc : acc[c];
-                if (DOT) dot += (double)uc * (double)y;
-            } else if (MODE == ST_RESID) {
-                const T Ku = fixed ? u[d] : acc[c];
-                y = f[d] - Ku;
-                if (DOT) dot += (double)y * (double)y;
-            } else if (MODE == ST_JACOBI) {
-                const T uc = u[d];
-                const T Ku = fixed ? uc : acc[c];
-                const T D = fixed ? T(1) : dg[c];
-                y = uc + omega * (f[d] - Ku) / D;
-                if (DOT) dot += (double)f[d] * (double)y;
-            } else {  // ST_JACOBI0
-                const T D = fixed ? T(1) : dg[c];
-                y = omega * f[d] / D;
-                if (DOT) dot += (double)f[d] * (double)y;
-            }
-            out[d] = y;
+            cu[c] = nu[c];
+            cf[c] = nf[c];
         }
+        T chu[3] = {hu[0], hu[1], hu[2]};
+        const unsigned chm = hm;
+        if (P + 1 <= kz1) fetch(P + 1);   // prefetch the next plane
+        // (2) publish this plane's masked u and the stashed contributions of plane P-2
+        if (NEEDU) {
+            T* us = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) us[c] = ((cm >> c) & 1u) ? T(0) : cu[c];
+            if (has_halo) {
+                T* hs = &sU[((b * (TY + 1) + hsy) * (TX + 1) + hsx) * 3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hs[c] = ((chm >> c) & 1u) ? T(0) : chu[c];
+            }
+            T* c0 = &sC[(((b * 3 + 0) * TY + ty) * TX + tx) * 3];
+            T* c1 = &sC[(((b * 3 + 1) * TY + ty) * TX + tx) * 3];
+            T* c2 = &sC[(((b * 3 + 2) * TY + ty) * TX + tx) * 3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                c0[c] = st10[c];
+                c1[c] = st01[c];
+                c2[c] = st11[c];
+            }
+        }
+        if (NEEDD) sE[(b * TY + ty) * TX + tx] = stE;
+        __syncthreads();
+        // (3) output node plane Q = P - 2
+        const int Q = P - 2;
+        if (out_ok && Q >= kz0 && Q < kz1) {
+            T y[3] = {T(0), T(0), T(0)};
+            if (NEEDU) {
+                const T* a0 = &sC[(((b * 3 + 0) * TY + ty) * TX + tx - 1) * 3];
+                const T* a1 = &sC[(((b * 3 + 1) * TY + ty - 1) * TX + tx) * 3];
+                const T* a2 = &sC[(((b * 3 + 2) * TY + ty - 1) * TX + tx - 1) * 3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
+            }
+            T D = T(1);
+            if (NEEDD) {
+                const T* e = &sE[b * TY * TX];
+                D = mk.kdiag * (e[ty * TX + tx] + e[ty * TX + tx - 1] + e[(ty - 1) * TX + tx] +
+                                e[(ty - 1) * TX + tx - 1]);
+            }
+            const long long n = (long long)Q * nplane + own_xy;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const bool fixed = (h2m >> c) & 1u;
+                T r;
+                if (MODE == ST_APPLY) {
+                    r = fixed ? h2u[c] : y[c];
+                    if (DOT) dot += (double)h2u[c] * (double)r;
+                } else if (MODE == ST_RESID) {
+                    r = h2f[c] - (fixed ? h2u[c] : y[c]);
+                    if (DOT) dot += (double)r * (double)r;
+                } else if (MODE == ST_JACOBI) {
+                    const T Ku = fixed ? h2u[c] : y[c];
+                    r = h2u[c] + omega * (h2f[c] - Ku) / (fixed ? T(1) : D);
+                    if (DOT) dot += (double)h2f[c] * (double)r;
+                } else {
+                    r = omega * h2f[c] / (fixed ? T(1) : D);
+                    if (DOT) dot += (double)h2f[c] * (double)r;
+                }
+                out[3 * n + c] = r;
+            }
+        }
+        // (4) face modes of plane P and the element of layer P-1 (plane P-1 completes)
+        if (P >= kz0 && P <= kz1) {
+            if (NEEDU) {
+                T fT[12];
+                const T* s00 = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
+                const T* s10 = s00 + 3;
+                const T* s01 = s00 + (TX + 1) * 3;
+                const T* s11 = s01 + 3;
+                face_forward<T>(s00, s10, s01, s11, fT);
+                T Bo[12], To[12];
+                if (cE != T(0)) {
+                    element_modal<T>(mk, cE, fB, fT, Bo, To);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) Bo[i] = To[i] = T(0);
+                }
+                T A[12];
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    A[i] = topPrev[i] + Bo[i];
+                    topPrev[i] = To[i];
+                    fB[i] = fT[i];
+                }
+                face_inverse<T>(A, st00, st10, st01, st11);
+            }
+            if (NEEDD) stE = Elast + cE;
+        } else if (NEEDU && P == kz0 - 1) {
+            const T* s00 = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
+            face_forward<T>(s00, s00 + 3, s00 + (TX + 1) * 3, s00 + (TX + 1) * 3 + 3, fB);
+        }
+        Elast = cE;
+        // shift the own-node history
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            h2u[c] = h1u[c];
+            h2f[c] = h1f[c];
+            h1u[c] = cu[c];
+            h1f[c] = cf[c];
+        }
+        h2m = h1m;
+        h1m = cm;
     }
     if (DOT) {
-        const double t = block_sum(dot, sred);
-        if (threadIdx.x == 0) partials[blockIdx.x] = t;
+        double v = dot;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int w = tid >> 5, l = tid & 31;
+        if (l == 0) sred[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            double t = (l < (TX * TY) / 32) ? sred[l] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (l == 0) partials[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+        }
     }
 }
 
-template <typename T, int MODE>
-void launch_mode(const Ctx& c, const Geom& g, const T* K0, const T* E, const uint8_t* mask, const T* u,
-                 const T* f, T* out, T omega, double* dot) {
-    const int threads = 256;
-    if (dot) {
-        k_stencil_gather<T, MODE, true><<<kRedBlocks, threads, 0, c.s>>>(K0, E, mask, u, f, out, g.nx, g.ny,
-                                                                       g.nz, omega, dot);
-    } else {
-        long long blocks = (g.nn + threads - 1) / threads;
-        if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-        k_stencil_gather<T, MODE, false><<<(unsigned)blocks, threads, 0, c.s>>>(K0, E, mask, u, f, out, g.nx,
-                                                                              g.ny, g.nz, omega, nullptr);
+template <typename T>
+constexpr size_t op_smem_bytes() {
+    return sizeof(T) * (2 * (kOpTY + 1) * (kOpTX + 1) * 3 + 2 * 3 * kOpTY * kOpTX * 3 + 2 * kOpTY * kOpTX);
+}
+
+template <typename T, int MODE, bool DOT>
+void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const T* u,
+               const T* f, T* out, T omega, double* dot) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_op<T, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_smem_bytes<T>());
+        attr = true;
     }
+    k_op<T, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, kOpTY), op_smem_bytes<T>(), c.s>>>(
+        mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot);
     TOPO_LAUNCH_CHECK(c);
+}
+
+template <typename T, int MODE>
+void launch_mode(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const T* u,
+                 const T* f, T* out, T omega, double* dot) {
+    if (dot) launch_op<T, MODE, true>(c, L, mk, E, mask, u, f, out, omega, dot);
+    else launch_op<T, MODE, false>(c, L, mk, E, mask, u, f, out, omega, nullptr);
 }
 
 // Dense assembly of the coarsest operator with identity Dirichlet rows.
@@ -195,20 +321,36 @@ __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double*
 
 }  // namespace
 
-template <typename T>
-void stencil(const Ctx& c, int mode, const Geom& g, const T* K0, const T* E, const uint8_t* mask, const T* u,
-             const T* f, T* out, T omega, double* dot) {
-    switch (mode) {
-        case ST_APPLY: launch_mode<T, ST_APPLY>(c, g, K0, E, mask, u, f, out, omega, dot); break;
-        case ST_JACOBI: launch_mode<T, ST_JACOBI>(c, g, K0, E, mask, u, f, out, omega, dot); break;
-        case ST_RESID: launch_mode<T, ST_RESID>(c, g, K0, E, mask, u, f, out, omega, dot); break;
-        default: launch_mode<T, ST_JACOBI0>(c, g, K0, E, mask, u, f, out, omega, dot); break;
-    }
+OpLaunch op_launch(const Geom& g) {
+    OpLaunch L;
+    L.g = g;
+    L.gx = (g.nx + 1 + kOpTX - 2) / (kOpTX - 1);
+    L.gy = (g.ny + 1 + kOpTY - 2) / (kOpTY - 1);
+    const long long xy = (long long)L.gx * L.gy;
+    const int NZ = g.nz + 1;
+    const long long gz_target = (4096 + xy - 1) / xy;
+    int cz = (int)((NZ + gz_target - 1) / gz_target);
+    cz = cz < 8 ? (NZ < 8 ? NZ : 8) : cz;
+    L.cz = cz;
+    L.gz = (NZ + cz - 1) / cz;
+    return L;
 }
-template void stencil<double>(const Ctx&, int, const Geom&, const double*, const double*, const uint8_t*,
-                              const double*, const double*, double*, double, double*);
-template void stencil<float>(const Ctx&, int, const Geom&, const float*, const float*, const uint8_t*,
-                             const float*, const float*, float*, float, double*);
+
+template <typename T>
+int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
+            const T* u, const T* f, T* out, T omega, double* dot) {
+    switch (mode) {
+        case ST_APPLY: launch_mode<T, ST_APPLY>(c, L, mk, E, mask, u, f, out, omega, dot); break;
+        case ST_JACOBI: launch_mode<T, ST_JACOBI>(c, L, mk, E, mask, u, f, out, omega, dot); break;
+        case ST_RESID: launch_mode<T, ST_RESID>(c, L, mk, E, mask, u, f, out, omega, dot); break;
+        default: launch_mode<T, ST_JACOBI0>(c, L, mk, E, mask, u, f, out, omega, dot); break;
+    }
+    return L.gx * L.gy * L.gz;
+}
+template int stencil<double>(const Ctx&, int, const OpLaunch&, const ModalK<double>&, const double*, const uint8_t*,
+                             const double*, const double*, double*, double, double*);
+template int stencil<float>(const Ctx&, int, const OpLaunch&, const ModalK<float>&, const float*, const uint8_t*,
+                            const float*, const float*, float*, float, double*);
 
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
                      double* A, int npad) {
