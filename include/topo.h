@@ -66,7 +66,7 @@ typedef struct {
     int pre, post;      /* Jacobi sweeps before / after the coarse correction (2,2) */
     double omega;       /* Jacobi damping (0.35); must be < 2/5.318 for an SPD V-cycle */
     int precision;      /* topo_precision (TOPO_FP64)                               */
-    double inner_tol;   /* residual reduction asked of each inner FP32 solve (1e-2) */
+    double inner_tol;   /* residual reduction asked of each inner FP32 solve (1e-4) */
     int inner_max_it;   /* iteration cap of each inner solve (500)                 */
     int max_refine;     /* cap on outer refinement steps (12)                      */
 } topo_params;

@@ -32,7 +32,7 @@ class Params:
     post: int = 2
     omega: float = 0.35
     precision: int = L.TOPO_FP64
-    inner_tol: float = 1e-2
+    inner_tol: float = 1e-4
     inner_max_it: int = 500
     max_refine: int = 12
 

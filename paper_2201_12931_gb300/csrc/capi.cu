@@ -230,7 +230,8 @@ topo_status prepare_filter(topo_grid* h, double r) {
     const Geom& g = h->lev[0].g;
     filter_launch(c, g, h->offs, h->wts, h->noffs, nullptr, h->S_cache, 2, nullptr);
     fill(c, g.ne, h->xnew_work, 1.0);
-    filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dv_cache, 1, h->S_cache);
+    divide(c, g.ne, h->xnew_work, h->S_cache, h->xnew_work);
+    filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dv_cache, 1, nullptr);
     CK(h, cudaStreamSynchronize(h->stream));   // host vectors above go out of scope
     h->S_radius = r;
     return TOPO_OK;
@@ -295,7 +296,7 @@ topo_status topo_default_params(topo_params* p) {
     p->post = 2;
     p->omega = 0.35;
     p->precision = TOPO_FP64;
-    p->inner_tol = 1e-2;
+    p->inner_tol = 1e-4;
     p->inner_max_it = 500;
     p->max_refine = 12;
     return TOPO_OK;
@@ -453,6 +454,7 @@ topo_status topo_set_bc_loads(topo_handle h, const uint8_t* fixed_dev, const dou
     const long long n0 = 3 * h->lev[0].g.nn;
     masked_copy_load(c, h->lev[0].g.nn, h->lev[0].mask, f_dev, h->f);
     CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * n0, h->stream));
+    h->x_zero = true;
     dot_partials<double, double>(c, n0, h->f, h->f, h->partials);
     reduce_to(c, h->partials, kRedBlocks, &h->sc->ff);
     CK(h, cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
@@ -485,10 +487,13 @@ topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it, double* 
     if (ff == 0.0) {
         CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * 3 * h->lev[0].g.nn, h->stream));
         h->stats.outer_steps = 0;
+        h->x_zero = true;
     } else if (fp64) {
         st = solve_fp64(h, rel_tol, max_it, &iters, &relres);
+        h->x_zero = false;
     } else {
         st = solve_mixed(h, rel_tol, max_it, &iters, &relres);
+        h->x_zero = false;
     }
     if (u_dev_out)
         CK(h, cudaMemcpyAsync(u_dev_out, h->x, sizeof(double) * 3 * h->lev[0].g.nn, cudaMemcpyDeviceToDevice,
@@ -514,7 +519,7 @@ topo_status topo_compliance_and_sensitivity(topo_handle h, double* C_out, double
     const Ctx c = h->ctx();
     const Geom& g = h->lev[0].g;
     element_energy_sens(c, g, h->modal, h->x, h->lev[0].rho, h->prm.E0, h->prm.Emin, h->prm.penal,
-                        dc_dev_out ? dc_dev_out : h->dc_work, h->partials);
+                        dc_dev_out ? dc_dev_out : h->dc_work, h->partials, h->prm.precision != TOPO_FP64);
     reduce_to(c, h->partials, kRedBlocks, h->dtmp);
     if (C_out) {
         CK(h, cudaMemcpyAsync(C_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -530,7 +535,14 @@ topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* o
     if (!in_dev || !out_dev || in_dev == out_dev) return fail(h, TOPO_BADARG, "bad pointers");
     s = prepare_filter(h, r);
     if (s != TOPO_OK) return s;
-    filter_launch(h->ctx(), h->lev[0].g, h->offs, h->wts, h->noffs, in_dev, out_dev, transpose ? 1 : 0, h->S_cache);
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    if (transpose) {
+        divide(c, g.ne, in_dev, h->S_cache, h->xnew_work);
+        filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, out_dev, 1, nullptr);
+    } else {
+        filter_launch(c, g, h->offs, h->wts, h->noffs, in_dev, out_dev, 0, nullptr);
+    }
     CK(h, cudaGetLastError());
     return TOPO_OK;
 }
@@ -546,8 +558,9 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
     if (s != TOPO_OK) return s;
     const Ctx c = h->ctx();
     const Geom& g = h->lev[0].g;
-    filter_launch(c, g, h->offs, h->wts, h->noffs, dc_dev, h->dc_work, 1, h->S_cache);
-    oc_prepare(c, g.ne, h->dc_work, h->dc_work);
+    divide(c, g.ne, dc_dev, h->S_cache, h->xnew_work);
+    filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dc_work, 1, nullptr);
+    oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, h->dc_work);
     const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
     const double init[8] = {l1, l2, 0.5 * (l1 + l2), (l2 - l1) / (l1 + l2) > tol ? 0.0 : 1.0, 0.0, 0.5 * (l1 + l2),
                             0.0, 0.0};
@@ -688,6 +701,7 @@ topo_status topo_reset_solution(topo_handle h) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
     CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * 3 * h->lev[0].g.nn, h->stream));
+    h->x_zero = true;
     return TOPO_OK;
 }
 

@@ -107,6 +107,7 @@ struct topo_grid {
     double* dtmp = nullptr;         // device scratch scalars
     int* dflag = nullptr;           // device: density out of [0,1] seen
     bool coarse_dirty = true;
+    bool x_zero = true;             // warm start is u = 0 (initial residual is f)
     // launch timing of fine-level operator kernels (topo_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;     // 2 per record
@@ -138,8 +139,9 @@ int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, cons
             const T* u, const T* f, T* out, T omega, double* dot_partials);
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
                      double* A, int npad);
+// low = true: FP32 modal contraction of FP64-relative displacements (mixed modes)
 void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
-                         double E0, double Emin, double penal, double* dc_out, double* partials);
+                         double E0, double Emin, double penal, double* dc_out, double* partials, bool low);
 
 // ---- transfer.cu ---------------------------------------------------------
 template <typename T>
@@ -182,10 +184,12 @@ template <typename T>
 void coarse_apply(const Ctx& c, int n, int npad, const T* W, const T* WT, const T* rhs, T* y, T* out);
 
 // ---- filter_oc.cu --------------------------------------------------------
-// mode 0: filter, 1: transpose (needs S), 2: write the weight sums S
+// mode 0: filter, 1: transpose of an input already divided by S, 2: weight sums S
 void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs, const double* in,
                    double* out, int mode, const double* S);
-void oc_prepare(const Ctx& c, long long ne, const double* dct, double* num);
+void divide(const Ctx& c, long long n, const double* a, const double* b, double* out);
+// q = x sqrt(max(-dc~, 1e-30) / dv~)
+void oc_prepare(const Ctx& c, long long ne, const double* x, const double* dct, const double* dv, double* q);
 void oc_bisect_step(const Ctx& c, long long ne, const double* x, const double* num, const double* dv,
                     double move, double* partials, double* lam_state);
 void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state, double volfrac_ne,

@@ -46,7 +46,7 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 }
 
 // mode 0: out_e = sum_d w_d in[e+d] / S_e (S_e on the fly)
-// mode 1: out_i = sum_d w_d in[i+d] / S[i+d]
+// mode 1: out_i = sum_d w_d in[i+d]   with in = g / S already divided
 // mode 2: out_e = S_e
 template <int MODE>
 __global__ void __launch_bounds__(256) k_filter(const int4* __restrict__ offs, const double* __restrict__ wts,
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_filter(const int4* __restrict__ offs, c
                 acc += w * in[nb];
                 ws += w;
             } else if (MODE == 1) {
-                acc += w * (in[nb] / S[nb]);
+                acc += w * in[nb];   // in = g / S, formed by k_divide
             } else {
                 ws += w;
             }
@@ -84,16 +84,26 @@ __global__ void __launch_bounds__(256) k_filter(const int4* __restrict__ offs, c
     }
 }
 
-__global__ void k_oc_prepare(long long ne, const double* __restrict__ dct, double* __restrict__ num) {
+__global__ void k_divide(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                         double* __restrict__ out) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = a[e] / b[e];
+}
+
+// q_e = x_e sqrt(max(-dc~_e, 1e-30) / dv~_e): the part of the OC candidate
+// x (B)^(1/2), B = -dc~ / (lambda dv~), that does not depend on lambda
+__global__ void k_oc_prepare(long long ne, const double* __restrict__ x, const double* __restrict__ dct,
+                             const double* __restrict__ dv, double* __restrict__ q) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= ne) return;
-    num[e] = fmax(-dct[e], 1e-30);
+    q[e] = x[e] * sqrt(fmax(-dct[e], 1e-30) / dv[e]);
 }
 
 // lam state: [0] l1, [1] l2, [2] lmid (next to evaluate), [3] done, [4] steps, [5] last lmid
-__device__ __forceinline__ double oc_candidate(double x, double num, double dv, double lam, double move) {
-    const double cand = x * sqrt(num / (lam * dv));
-    return fmax(0.0, fmax(x - move, fmin(1.0, fmin(x + move, cand))));
+// candidate clamped to the move limits and [0, 1]; s = lambda^(-1/2)
+__device__ __forceinline__ double oc_candidate(double x, double q, double s, double move) {
+    return fmax(0.0, fmax(x - move, fmin(1.0, fmin(x + move, q * s))));
 }
 
 __global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __restrict__ x, const double* __restrict__ num,
@@ -104,10 +114,10 @@ __global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __r
         if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
         return;
     }
-    const double lm = lam[2];
+    const double sl = rsqrt(lam[2]);
     double s = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
-        s += dv[e] * oc_candidate(x[e], num[e], dv[e], lm, move);
+        s += dv[e] * oc_candidate(x[e], num[e], sl, move);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -135,11 +145,11 @@ __global__ void __launch_bounds__(256) k_oc_write(long long ne, double* __restri
                                                   const double* __restrict__ dv, double move, const double* __restrict__ lam,
                                                   double* __restrict__ partials) {
     __shared__ double sh[32];
-    const double lm = lam[5];
+    const double sl = rsqrt(lam[5]);
     double m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
         const double xo = x[e];
-        const double xn = oc_candidate(xo, num[e], dv[e], lm, move);
+        const double xn = oc_candidate(xo, num[e], sl, move);
         m = fmax(m, fabs(xn - xo));
         x[e] = xn;
     }
@@ -168,8 +178,13 @@ void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* 
     TOPO_LAUNCH_CHECK(c);
 }
 
-void oc_prepare(const Ctx& c, long long ne, const double* dct, double* num) {
-    k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, dct, num);
+void divide(const Ctx& c, long long n, const double* a, const double* b, double* out) {
+    k_divide<<<grid_for(n, 256), 256, 0, c.s>>>(n, a, b, out);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_prepare(const Ctx& c, long long ne, const double* x, const double* dct, const double* dv, double* q) {
+    k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, x, dct, dv, q);
     TOPO_LAUNCH_CHECK(c);
 }
 

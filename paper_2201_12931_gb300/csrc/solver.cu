@@ -157,7 +157,12 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
     return it;
 }
 
+// r = f - K x in FP64 and ||r||^2; with x known to be zero, r = f.
 static double residual64(topo_grid* h) {
+    if (h->x_zero) {
+        cudaMemcpyAsync(h->r, h->f, sizeof(double) * 3 * h->lev[0].g.nn, cudaMemcpyDeviceToDevice, h->stream);
+        return h->host_sc[6];
+    }
     const int np = op_apply<double>(h, ST_RESID, 0, h->x, h->f, h->r, h->partials);
     reduce_to(h->ctx(), h->partials, np, &h->sc->rr);
     fetch_scalars(h);
@@ -174,6 +179,7 @@ int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres)
     for (;;) {
         double rr;
         it += pcg_core<double>(h, h->x, h->r, h->z, h->p, h->q, rr_true, tol * tol * ff, max_it - it, &status, &rr);
+        h->x_zero = false;
         rr_true = residual64(h);
         if (status != TOPO_OK || rr_true <= tol * tol * ff || restarts >= 4 || it >= max_it) break;
         ++restarts;
@@ -211,6 +217,7 @@ int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres
                                        max_it - total, &st, &rr_in);
         total += it;
         axpy_f32_into_f64(c, n, h->d32, h->x);
+        h->x_zero = false;
         ++outer;
         const double rr_new = residual64(h);
         if (st == TOPO_BREAKDOWN || !std::isfinite(rr_new)) {

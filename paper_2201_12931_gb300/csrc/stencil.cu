@@ -6,6 +6,8 @@
 //
 // Operator with Dirichlet rows: y = P_f K P_f u + (I - P_f) u, P_f zeroing the
 // fixed DOFs, K = sum_e E_e A_e^T K0 A_e (E_e already holds 2^l on level l).
+#include <type_traits>
+
 #include "common.cuh"
 #include "modal.cuh"
 #include "operator.cuh"
@@ -27,20 +29,45 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;   // valid in thread 0
 }
 
+// Shared-memory slots hold one node's three components padded to four, so a
+// slot moves with one 128-bit access (FP32) or a 128 + 64-bit pair (FP64).
+__device__ __forceinline__ void st3(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void ld3(const float* p, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+}
+__device__ __forceinline__ void st3(double* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    p[2] = v[2];
+}
+__device__ __forceinline__ void ld3(const double* p, double* v) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = p[2];
+}
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Element-column z-march operator kernel; see operator.cuh for the scheme.
+// The per-plane body is a generic lambda called with a compile-time buffer
+// parity B = P & 1, so that double buffers and the two-plane register history
+// are addressed statically (no register moves, no dynamic indexing).
 template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(kOpTX * kOpTY) k_op(ModalK<T> mk, const T* __restrict__ E,
-                                                      const uint8_t* __restrict__ mask, const T* __restrict__ u,
-                                                      const T* __restrict__ f, T* __restrict__ out, int nx, int ny,
-                                                      int nz, int cz, T omega, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
+    k_op(const ModalK<T> mk, const T* __restrict__ E, const uint8_t* __restrict__ mask, const T* __restrict__ u,
+         const T* __restrict__ f, T* __restrict__ out, const int nx, const int ny, const int nz, const int cz,
+         const T omega, double* __restrict__ partials) {
     constexpr int TX = kOpTX, TY = kOpTY;
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
     constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
     constexpr bool NEEDF = (MODE != ST_APPLY);
+    constexpr int nU = (TY + 1) * (TX + 1) * 4, nC = 3 * TY * TX * 4, nEs = TY * TX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sU = reinterpret_cast<T*>(smem_raw);        // [2][TY+1][TX+1][3]   masked u of a node plane
-    T* sC = sU + 2 * (TY + 1) * (TX + 1) * 3;      // [2][3][TY][TX][3]     corner contributions 10, 01, 11
-    T* sE = sC + 2 * 3 * TY * TX * 3;              // [2][TY][TX]           column modulus sums
     __shared__ double sred[32];
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -52,176 +79,178 @@ __global__ void __launch_bounds__(kOpTX * kOpTY) k_op(ModalK<T> mk, const T* __r
     const bool node_ok = in >= 0 && in < NX && jn >= 0 && jn < NY;
     const bool col_ok = in >= 0 && in < nx && jn >= 0 && jn < ny;
     const bool out_ok = tx >= 1 && ty >= 1 && node_ok;
-    // one halo node (+x column, +y row, +x+y corner) per thread with tid < TX + TY + 1
-    int hsx = TX, hsy = TY;
-    if (tid < TY + 1) { hsx = TX; hsy = tid; }
-    else if (tid < TY + 1 + TX) { hsx = tid - TY - 1; hsy = TY; }
     const bool has_halo = tid < TY + 1 + TX;
+    const int hsx = tid < TY + 1 ? TX : tid - TY - 1;
+    const int hsy = tid < TY + 1 ? tid : TY;
     const int hx = i0 - 1 + hsx, hy = j0 - 1 + hsy;
     const bool halo_ok = has_halo && hx >= 0 && hx < NX && hy >= 0 && hy < NY;
     const long long nplane = (long long)NX * NY;
-    const long long own_xy = node_ok ? (long long)in + (long long)NX * jn : 0;
-    const long long halo_xy = halo_ok ? (long long)hx + (long long)NX * hy : 0;
-    const long long col_xy = col_ok ? (long long)in + (long long)nx * jn : 0;
-    const long long eplane = (long long)nx * ny;
+    const int own_xy = node_ok ? in + NX * jn : 0;
+    const int halo_xy = halo_ok ? hx + NX * hy : 0;
+    const int col_xy = col_ok ? in + nx * jn : 0;
+    const int uoff = (ty * (TX + 1) + tx) * 4;      // own slot in a plane buffer
+    const int hoff = (hsy * (TX + 1) + hsx) * 4;    // halo slot
+    const int coff = (ty * TX + tx) * 4;            // own slot in a contribution buffer
 
-    T fB[12], topPrev[12];
+    T fb[2][12], top[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) fB[i] = topPrev[i] = T(0);
-    T st00[3] = {T(0), T(0), T(0)}, st10[3] = {T(0), T(0), T(0)}, st01[3] = {T(0), T(0), T(0)},
-      st11[3] = {T(0), T(0), T(0)};
-    T stE = T(0);
-    // own-node history (raw u, mask, f) of planes P-1 (h1) and P-2 (h2)
-    T h1u[3] = {T(0), T(0), T(0)}, h2u[3] = {T(0), T(0), T(0)};
-    T h1f[3] = {T(0), T(0), T(0)}, h2f[3] = {T(0), T(0), T(0)};
-    unsigned h1m = 0, h2m = 0;
-    T Elast = T(0);       // E of own column, layer P-2
+    for (int i = 0; i < 12; ++i) fb[0][i] = fb[1][i] = top[i] = T(0);
+    T st00[3] = {}, st10[3] = {}, st01[3] = {}, st11[3] = {};
+    T stE = T(0), Elast = T(0);
+    T hu[2][3] = {}, hf[2][3] = {};
+    unsigned hm[2] = {0u, 0u};
     double dot = 0.0;
+    T nu[3] = {}, nf[3] = {}, hv[3] = {}, nE = T(0);
+    unsigned nm = 0u, nhm = 0u;
+    long long ob = (long long)(kz0 - 1) * nplane;    // plane offset of the next fetch
 
-    // prefetched data of plane P
-    T nu[3] = {T(0), T(0), T(0)}, nf[3] = {T(0), T(0), T(0)}, hu[3] = {T(0), T(0), T(0)};
-    unsigned nm = 0, hm = 0;
-    T nE = T(0);          // E of own column, layer P-1
     auto fetch = [&](int P) {
         const bool pin = P >= 0 && P <= nz;
-        const long long ob = (long long)P * nplane;
         if (NEEDU || NEEDF) {
             const bool ok = pin && node_ok;
-            nm = ok ? mask[ob + own_xy] : 0u;
+            const long long n = ob + own_xy;
+            nm = ok ? mask[n] : 0u;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (NEEDU) nu[c] = ok ? u[3 * (ob + own_xy) + c] : T(0);
-                if (NEEDF) nf[c] = ok ? f[3 * (ob + own_xy) + c] : T(0);
+                if (NEEDU) nu[c] = ok ? u[3 * n + c] : T(0);
+                if (NEEDF) nf[c] = ok ? f[3 * n + c] : T(0);
             }
         }
         if (NEEDU) {
             const bool okh = pin && halo_ok;
-            hm = okh ? mask[ob + halo_xy] : 0u;
+            const long long n = ob + halo_xy;
+            nhm = okh ? mask[n] : 0u;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) hu[c] = okh ? u[3 * (ob + halo_xy) + c] : T(0);
+            for (int c = 0; c < 3; ++c) hv[c] = okh ? u[3 * n + c] : T(0);
         }
-        const int L = P - 1;
-        nE = (col_ok && L >= 0 && L < nz) ? E[(long long)L * eplane + col_xy] : T(0);
+        nE = (col_ok && P >= 1 && P <= nz) ? E[(long long)(P - 1) * nx * ny + col_xy] : T(0);
+        ob += nplane;
     };
 
-    fetch(kz0 - 1);
-    for (int P = kz0 - 1; P <= kz1 + 1; ++P) {
-        const int b = P & 1;
-        // current plane data
-        T cu[3], cf[3];
-        const unsigned cm = nm;
+    auto step = [&](auto Bc, int P) {
+        constexpr int B = decltype(Bc)::value;
+        T* const U = reinterpret_cast<T*>(smem_raw) + B * nU;
+        T* const Cb = reinterpret_cast<T*>(smem_raw) + 2 * nU + B * nC;
+        T* const Eb = reinterpret_cast<T*>(smem_raw) + 2 * nU + 2 * nC + B * nEs;
+        const unsigned cm = nm, chm = nhm;
         const T cE = nE;
+        T cu[3], cf[3], ch[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             cu[c] = nu[c];
             cf[c] = nf[c];
+            ch[c] = hv[c];
         }
-        T chu[3] = {hu[0], hu[1], hu[2]};
-        const unsigned chm = hm;
-        if (P + 1 <= kz1) fetch(P + 1);   // prefetch the next plane
-        // (2) publish this plane's masked u and the stashed contributions of plane P-2
+        if (P + 1 <= kz1) fetch(P + 1);
+        // publish plane P (masked) and the stashed contributions of plane P - 2
         if (NEEDU) {
-            T* us = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
+            T mu[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) us[c] = ((cm >> c) & 1u) ? T(0) : cu[c];
+            for (int c = 0; c < 3; ++c) mu[c] = ((cm >> c) & 1u) ? T(0) : cu[c];
+            st3(U + uoff, mu);
             if (has_halo) {
-                T* hs = &sU[((b * (TY + 1) + hsy) * (TX + 1) + hsx) * 3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) hs[c] = ((chm >> c) & 1u) ? T(0) : chu[c];
+                for (int c = 0; c < 3; ++c) mu[c] = ((chm >> c) & 1u) ? T(0) : ch[c];
+                st3(U + hoff, mu);
             }
-            T* c0 = &sC[(((b * 3 + 0) * TY + ty) * TX + tx) * 3];
-            T* c1 = &sC[(((b * 3 + 1) * TY + ty) * TX + tx) * 3];
-            T* c2 = &sC[(((b * 3 + 2) * TY + ty) * TX + tx) * 3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                c0[c] = st10[c];
-                c1[c] = st01[c];
-                c2[c] = st11[c];
-            }
+            st3(Cb + coff, st10);
+            st3(Cb + nC / 3 + coff, st01);
+            st3(Cb + 2 * (nC / 3) + coff, st11);
         }
-        if (NEEDD) sE[(b * TY + ty) * TX + tx] = stE;
+        if (NEEDD) Eb[ty * TX + tx] = stE;
         __syncthreads();
-        // (3) output node plane Q = P - 2
+        // output node plane Q = P - 2 (history slot B)
         const int Q = P - 2;
         if (out_ok && Q >= kz0 && Q < kz1) {
             T y[3] = {T(0), T(0), T(0)};
             if (NEEDU) {
-                const T* a0 = &sC[(((b * 3 + 0) * TY + ty) * TX + tx - 1) * 3];
-                const T* a1 = &sC[(((b * 3 + 1) * TY + ty - 1) * TX + tx) * 3];
-                const T* a2 = &sC[(((b * 3 + 2) * TY + ty - 1) * TX + tx - 1) * 3];
+                T a0[3], a1[3], a2[3];
+                ld3(Cb + coff - 4, a0);
+                ld3(Cb + nC / 3 + coff - TX * 4, a1);
+                ld3(Cb + 2 * (nC / 3) + coff - TX * 4 - 4, a2);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
             }
-            T D = T(1);
+            T rD = T(1);
             if (NEEDD) {
-                const T* e = &sE[b * TY * TX];
-                D = mk.kdiag * (e[ty * TX + tx] + e[ty * TX + tx - 1] + e[(ty - 1) * TX + tx] +
-                                e[(ty - 1) * TX + tx - 1]);
+                const T* e = Eb + ty * TX + tx;
+                rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
-            const long long n = (long long)Q * nplane + own_xy;
+            T* o = out + 3 * ((long long)Q * nplane + own_xy);
+            const unsigned m2 = hm[B];
+            T d32 = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const bool fixed = (h2m >> c) & 1u;
+                const bool fixed = (m2 >> c) & 1u;
+                const T uo = hu[B][c], fo = hf[B][c];
                 T r;
                 if (MODE == ST_APPLY) {
-                    r = fixed ? h2u[c] : y[c];
-                    if (DOT) dot += (double)h2u[c] * (double)r;
+                    r = fixed ? uo : y[c];
+                    if (DOT) d32 += uo * r;
                 } else if (MODE == ST_RESID) {
-                    r = h2f[c] - (fixed ? h2u[c] : y[c]);
-                    if (DOT) dot += (double)r * (double)r;
+                    r = fo - (fixed ? uo : y[c]);
+                    if (DOT) d32 += r * r;
                 } else if (MODE == ST_JACOBI) {
-                    const T Ku = fixed ? h2u[c] : y[c];
-                    r = h2u[c] + omega * (h2f[c] - Ku) / (fixed ? T(1) : D);
-                    if (DOT) dot += (double)h2f[c] * (double)r;
+                    r = fixed ? uo + omega * (fo - uo) : uo + omega * (fo - y[c]) * rD;
+                    if (DOT) d32 += fo * r;
                 } else {
-                    r = omega * h2f[c] / (fixed ? T(1) : D);
-                    if (DOT) dot += (double)h2f[c] * (double)r;
+                    r = omega * fo * (fixed ? T(1) : rD);
+                    if (DOT) d32 += fo * r;
                 }
-                out[3 * n + c] = r;
+                o[c] = r;
             }
+            if (DOT) dot += (double)d32;
         }
-        // (4) face modes of plane P and the element of layer P-1 (plane P-1 completes)
+        // face modes of plane P; element of layer P - 1; plane P - 1 completes
         if (P >= kz0 && P <= kz1) {
             if (NEEDU) {
-                T fT[12];
-                const T* s00 = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
-                const T* s10 = s00 + 3;
-                const T* s01 = s00 + (TX + 1) * 3;
-                const T* s11 = s01 + 3;
-                face_forward<T>(s00, s10, s01, s11, fT);
+                T c00[3], c10[3], c01[3], c11[3];
+                ld3(U + uoff, c00);
+                ld3(U + uoff + 4, c10);
+                ld3(U + uoff + (TX + 1) * 4, c01);
+                ld3(U + uoff + (TX + 1) * 4 + 4, c11);
+                face_forward<T>(c00, c10, c01, c11, fb[B]);
                 T Bo[12], To[12];
-                if (cE != T(0)) {
-                    element_modal<T>(mk, cE, fB, fT, Bo, To);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 12; ++i) Bo[i] = To[i] = T(0);
-                }
+                element_modal<T>(mk, cE, fb[B ^ 1], fb[B], Bo, To);
                 T A[12];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) {
-                    A[i] = topPrev[i] + Bo[i];
-                    topPrev[i] = To[i];
-                    fB[i] = fT[i];
+                    A[i] = top[i] + Bo[i];
+                    top[i] = To[i];
                 }
                 face_inverse<T>(A, st00, st10, st01, st11);
             }
             if (NEEDD) stE = Elast + cE;
         } else if (NEEDU && P == kz0 - 1) {
-            const T* s00 = &sU[((b * (TY + 1) + ty) * (TX + 1) + tx) * 3];
-            face_forward<T>(s00, s00 + 3, s00 + (TX + 1) * 3, s00 + (TX + 1) * 3 + 3, fB);
+            T c00[3], c10[3], c01[3], c11[3];
+            ld3(U + uoff, c00);
+            ld3(U + uoff + 4, c10);
+            ld3(U + uoff + (TX + 1) * 4, c01);
+            ld3(U + uoff + (TX + 1) * 4 + 4, c11);
+            face_forward<T>(c00, c10, c01, c11, fb[B]);
         }
         Elast = cE;
-        // shift the own-node history
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            h2u[c] = h1u[c];
-            h2f[c] = h1f[c];
-            h1u[c] = cu[c];
-            h1f[c] = cf[c];
+            hu[B][c] = cu[c];
+            hf[B][c] = cf[c];
         }
-        h2m = h1m;
-        h1m = cm;
+        hm[B] = cm;
+    };
+
+    using B0 = std::integral_constant<int, 0>;
+    using B1 = std::integral_constant<int, 1>;
+    fetch(kz0 - 1);
+    int P = kz0 - 1;
+    if (P & 1) {
+        step(B1{}, P);
+        ++P;
     }
+    for (; P + 1 <= kz1 + 1; P += 2) {
+        step(B0{}, P);
+        step(B1{}, P + 1);
+    }
+    if (P <= kz1 + 1) step(B0{}, P);
     if (DOT) {
         double v = dot;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -238,7 +267,7 @@ __global__ void __launch_bounds__(kOpTX * kOpTY) k_op(ModalK<T> mk, const T* __r
 
 template <typename T>
 constexpr size_t op_smem_bytes() {
-    return sizeof(T) * (2 * (kOpTY + 1) * (kOpTX + 1) * 3 + 2 * 3 * kOpTY * kOpTX * 3 + 2 * kOpTY * kOpTX);
+    return sizeof(T) * (2 * (kOpTY + 1) * (kOpTX + 1) * 4 + 2 * 3 * kOpTY * kOpTX * 4 + 2 * kOpTY * kOpTX);
 }
 
 template <typename T, int MODE, bool DOT>
@@ -285,11 +314,26 @@ __global__ void k_assemble_diag(const uint8_t* __restrict__ mask, double* __rest
     if (d >= n || ((mask[d / 3] >> (d % 3)) & 1u)) A[(long long)d * npad + d] = 1.0;
 }
 
+// rho^p by repeated multiplication for integer p (FP64 pow is slow on GB300)
+__device__ __forceinline__ double ipow(double r, double p, int ip) {
+    if (ip >= 0) {
+        double v = 1.0;
+        for (int i = 0; i < ip; ++i) v *= r;
+        return v;
+    }
+    return pow(r, p);
+}
+
 // Element energy u_e^T K0 u_e in the modal (Walsh-Hadamard) basis, compliance
 // partial sums sum_e E_e se_e and the sensitivity -p rho^(p-1) (E0-Emin) se_e.
+// LOW = true (mixed-precision handles): the corner-0 displacement is
+// subtracted in FP64 (K0 annihilates translations, so the energy is
+// unchanged), and the small relative displacements are transformed and
+// contracted in FP32; the compliance is still accumulated in FP64.
+template <bool LOW>
 __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double* __restrict__ u,
                                                      const double* __restrict__ rho, int nx, int ny, int nz,
-                                                     double E0, double Emin, double penal,
+                                                     double E0, double Emin, double penal, int ipenal,
                                                      double* __restrict__ dc, double* __restrict__ partials) {
     __shared__ double sred[32];
     const long long ne = (long long)nx * ny * nz;
@@ -300,20 +344,39 @@ __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double*
         const int i = (int)(e % nx);
         const long long t = e / nx;
         const int j = (int)(t % ny), k = (int)(t / ny);
-        double ue[24];
+        double se;
+        if (LOW) {
+            const long long n0 = i + (long long)NX * (j + (long long)NY * k);
+            const double r0 = u[3 * n0], r1 = u[3 * n0 + 1], r2 = u[3 * n0 + 2];
+            float ue[24];
+            ue[0] = ue[1] = ue[2] = 0.f;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
+            for (int a = 1; a < 8; ++a) {
+                const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
+                ue[3 * a + 0] = (float)(u[3 * nd + 0] - r0);
+                ue[3 * a + 1] = (float)(u[3 * nd + 1] - r1);
+                ue[3 * a + 2] = (float)(u[3 * nd + 2] - r2);
+            }
+            float m[24];
+            modal_forward(ue, m);
+            se = (double)modal_energy<float>(mc, m);
+        } else {
+            double ue[24];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nd + c];
+            for (int a = 0; a < 8; ++a) {
+                const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nd + c];
+            }
+            double m[24];
+            modal_forward(ue, m);
+            se = modal_energy(mc, m);
         }
-        double m[24];
-        modal_forward(ue, m);
-        const double se = modal_energy(mc, m);
         const double r = rho[e];
-        const double Ee = Emin + pow(r, penal) * (E0 - Emin);
+        const double rp1 = ipenal >= 1 ? ipow(r, penal - 1.0, ipenal - 1) : pow(r, penal - 1.0);
+        const double Ee = Emin + rp1 * r * (E0 - Emin);
         csum += Ee * se;
-        if (dc) dc[e] = -penal * pow(r, penal - 1.0) * (E0 - Emin) * se;
+        if (dc) dc[e] = -penal * rp1 * (E0 - Emin) * se;
     }
     const double tsum = block_sum(csum, sred);
     if (threadIdx.x == 0) partials[blockIdx.x] = tsum;
@@ -328,9 +391,11 @@ OpLaunch op_launch(const Geom& g) {
     L.gy = (g.ny + 1 + kOpTY - 2) / (kOpTY - 1);
     const long long xy = (long long)L.gx * L.gy;
     const int NZ = g.nz + 1;
-    const long long gz_target = (4096 + xy - 1) / xy;
+    // enough CTAs for ~4 waves of 2 resident CTAs on 152 SMs, but chunks of at
+    // least 16 planes (each chunk recomputes one layer and two exchange steps)
+    const long long gz_target = (1216 + xy - 1) / xy;
     int cz = (int)((NZ + gz_target - 1) / gz_target);
-    cz = cz < 8 ? (NZ < 8 ? NZ : 8) : cz;
+    cz = cz < 16 ? (NZ < 16 ? NZ : 16) : cz;
     L.cz = cz;
     L.gz = (NZ + cz - 1) / cz;
     return L;
@@ -362,8 +427,14 @@ void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double
 }
 
 void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
-                         double E0, double Emin, double penal, double* dc_out, double* partials) {
-    k_energy_sens<<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, dc_out, partials);
+                         double E0, double Emin, double penal, double* dc_out, double* partials, bool low) {
+    const int ip = (penal == (double)(int)penal && penal >= 1.0 && penal <= 16.0) ? (int)penal : -1;
+    if (low)
+        k_energy_sens<true><<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, ip, dc_out,
+                                                           partials);
+    else
+        k_energy_sens<false><<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, ip, dc_out,
+                                                            partials);
     TOPO_LAUNCH_CHECK(c);
 }
 

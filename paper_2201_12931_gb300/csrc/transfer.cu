@@ -109,14 +109,24 @@ __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__
     rc[E] = 0.125 * s;
 }
 
+// rho^p: repeated multiplication for integer p (FP64 pow is slow on this part)
+__device__ __forceinline__ double rpow(double r, double p, int ip) {
+    if (ip >= 0) {
+        double v = 1.0;
+        for (int i = 0; i < ip; ++i) v *= r;
+        return v;
+    }
+    return pow(r, p);
+}
+
 __global__ void k_simp(long long ne, const double* __restrict__ rho, double scale, double E0, double Emin,
-                       double penal, double* __restrict__ E64, float* __restrict__ E32, int* bad) {
+                       double penal, int ipenal, double* __restrict__ E64, float* __restrict__ E32, int* bad) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const double r = rho[e];
     if (!(r >= 0.0 && r <= 1.0)) atomicExch(bad, 1);
     const double rc = fmin(fmax(r, 0.0), 1.0);
-    const double E = scale * (Emin + pow(rc, penal) * (E0 - Emin));
+    const double E = scale * (Emin + rpow(rc, penal, ipenal) * (E0 - Emin));
     E64[e] = E;
     E32[e] = (float)E;
 }
@@ -177,7 +187,8 @@ void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c
 
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0, double Emin, double penal,
                  double* E64, float* E32, int* bad_flag) {
-    k_simp<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, rho, scale, E0, Emin, penal, E64, E32, bad_flag);
+    const int ip = (penal == (double)(int)penal && penal >= 0.0 && penal <= 16.0) ? (int)penal : -1;
+    k_simp<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, rho, scale, E0, Emin, penal, ip, E64, E32, bad_flag);
     TOPO_LAUNCH_CHECK(c);
 }
 

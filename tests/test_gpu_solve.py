@@ -1,9 +1,11 @@
 """GPU state solve, compliance and sensitivity against the oracle.
 
 Bars: relative L2 displacement error and relative compliance error <= 1e-6
-at rel_tol 1e-8, and <= 1e-9 at rel_tol 1e-12 (FP64); sensitivity max error
-<= 1e-5 relative to max |dc|.  Mixed precision is held to the same bars
-(the FP64 refinement loop reaches the FP64 residual target).
+at rel_tol 1e-8, and <= 1e-9 at rel_tol 1e-12 (FP64 path); sensitivity max
+error <= 1e-7 relative to max |dc| (FP64 path).  Mixed-precision handles
+reach the same displacement bars (the FP64 refinement loop reaches the FP64
+residual target) and contract the element energy in FP32 after an FP64
+translation shift: compliance <= 1e-7, sensitivity <= 1e-5.
 """
 import numpy as np
 import pytest
@@ -46,10 +48,14 @@ def test_solve_matches_oracle(dims, levels, problem, precision):
         assert res.status == 0, res
         assert res.relres <= tol
         assert np.linalg.norm(u - u_o) <= bar * np.linalg.norm(u_o)
-        assert abs(C - C_o) <= bar * abs(C_o)
-        assert np.abs(dc - dc_o).max() <= max(bar, 1e-7) * np.abs(dc_o).max()
+        # FP64 path: the solve's bar; mixed handles contract the element
+        # energy in FP32 (bars 1e-7 on C, 1e-5 on dc, stated per result)
+        c_bar = bar if precision == 0 else max(bar, 1e-7)
+        dc_bar = max(bar, 1e-7) if precision == 0 else 1e-5
+        assert abs(C - C_o) <= c_bar * abs(C_o)
+        assert np.abs(dc - dc_o).max() <= dc_bar * np.abs(dc_o).max()
         # energy identity C = f^T u on the GPU result
-        assert abs(C - pb.f @ u) <= 10 * tol * abs(C)
+        assert abs(C - pb.f @ u) <= max(10 * tol, 0.0 if precision == 0 else 1e-7) * abs(C)
 
 
 def test_uniform_density_cantilever_48():
