@@ -221,6 +221,25 @@ topo_status topo_profile_enable(topo_handle h, int on);
  * precision: index 0 = FP64 kernel, 1 = FP32 kernel (arrays of length 2). */
 topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms);
 
+/* Density filter for callers that cannot allocate GPU memory (no counterpart
+ * in the paper).  Same result as topo_filter on a handle of the same grid,
+ * without a handle: a framework whose caching allocator owns the device
+ * memory, or a loop that must not stall on the device-wide synchronisation
+ * of cudaMalloc/cudaFree, can call it at any point.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine; its scratch (weight sums,
+ * divided input, neighbour table) lives in one statically sized array of
+ * about 16 MiB that every GPU loading this library holds until the process
+ * exits.  The first call on a device looks up that array's address (make it
+ * before any stream capture).  Grids of at most 1,048,576 elements
+ * (nx*ny*nz) and radii 0 < r <= 6; larger grids return TOPO_BADARG with a
+ * message from topo_last_error(NULL).  in_dev/out_dev: device, nx*ny*nz FP64,
+ * must not overlap; stream: cudaStream_t (NULL = legacy default stream).
+ * All calls share the one array and leave their data in it: calls that can
+ * overlap on the GPU (on different streams) race and must be ordered by the
+ * caller.  Nothing in the array needs to start at zero. */
+topo_status topo_filter_noalloc(int nx, int ny, int nz, double r, const double* in_dev, double* out_dev,
+                                int transpose, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ _SIGS = {
     "topo_reset_solution": ([H], C.c_int),
     "topo_profile_enable": ([H, C.c_int], C.c_int),
     "topo_profile_read": ([H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)], C.c_int),
+    "topo_filter_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_double, P, P, C.c_int, C.c_void_p], C.c_int),
 }
 
 _lib = None

@@ -283,6 +283,8 @@ topo_status check_handle(topo_grid* h) {
 
 }  // namespace
 
+void topo::set_global_error(const std::string& msg) { g_create_err = msg; }
+
 extern "C" {
 
 topo_status topo_default_params(topo_params* p) {

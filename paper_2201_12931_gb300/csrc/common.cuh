@@ -184,6 +184,8 @@ template <typename T>
 void coarse_apply(const Ctx& c, int n, int npad, const T* W, const T* WT, const T* rhs, T* y, T* out);
 
 // ---- filter_oc.cu --------------------------------------------------------
+// message returned by topo_last_error(NULL)
+void set_global_error(const std::string& msg);
 // mode 0: filter, 1: transpose of an input already divided by S, 2: weight sums S
 void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs, const double* in,
                    double* out, int mode, const double* S);
