@@ -17,10 +17,10 @@ import numpy as np
 from .assemble import constrained_system, simp_modulus
 from .element import element_stiffness
 from .filter import density_filter
-from .multigrid import mgpcg_galerkin
+from .multigrid import homogenized_hierarchy, max_levels, mgpcg_galerkin, vcycle
 from .oc import oc_update
 from .sensitivity import compliance, element_energy, sensitivity
-from .solve import solve_dense, solve_sparse_direct
+from .solve import pcg, solve_dense, solve_sparse_direct
 
 
 def solve_state(dims, rho, fixed, f, nu=0.3, E0=1.0, Emin=1e-9, penal=3.0, tol=1e-12,
@@ -36,6 +36,18 @@ def solve_state(dims, rho, fixed, f, nu=0.3, E0=1.0, Emin=1e-9, penal=3.0, tol=1
         u = solve_dense(K, fb)
     elif method == "direct":
         u = solve_sparse_direct(K, fb)
+    elif method == "mgpcg_homog":
+        # PCG with the homogenized V-cycle (cheaper set-up than Galerkin
+        # products on large grids; the converged u does not depend on M)
+        H = homogenized_hierarchy(dims, rho, fixed, K0, max_levels(dims), E0, Emin, penal)
+        Lc = np.linalg.cholesky(H[-1].K.toarray())
+        import scipy.linalg as sla
+
+        def coarse(b):
+            return sla.solve_triangular(Lc.T, sla.solve_triangular(Lc, b, lower=True), lower=False)
+
+        u, it, rr = pcg(K, fb, lambda r: vcycle(H, r, coarse_solve=coarse), tol, 5000, x0)
+        info.update(iters=it, relres=rr)
     else:
         u, it, rr = mgpcg_galerkin(K, fb, dims, fixed, tol=tol, x0=x0)
         info.update(iters=it, relres=rr)

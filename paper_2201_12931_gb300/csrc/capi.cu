@@ -358,8 +358,9 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
         Level& lv = h->lev[l];
         lv.g = make_geom(nx >> l, ny >> l, nz >> l);
         lv.scale = (double)(1 << l);
-        lv.op = op_launch(lv.g);
-        h->npartials = std::max(h->npartials, lv.op.ctas());
+        lv.op32 = op_launch32(lv.g);
+        lv.op64 = op_launch64(lv.g);
+        h->npartials = std::max(h->npartials, std::max(lv.op32.ctas(), lv.op64.ctas()));
     }
     topo_status st;
 #define TRY(expr)                          \

@@ -50,7 +50,7 @@ struct VBuf {             // V-cycle work vectors of one level in one precision
 
 struct Level {
     Geom g;
-    OpLaunch op;
+    OpLaunch op32, op64;      // operator launch geometry per precision
     double scale = 1.0;       // 2^l
     double* rho = nullptr;    // homogenized density
     double* E64 = nullptr;    // 2^l * (Emin + rho^p (E0 - Emin))
@@ -133,7 +133,8 @@ enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3 };
 // out = op(u, f); with dot != nullptr also writes per-CTA partial sums of
 //   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
 // and returns the number of partials written.
-OpLaunch op_launch(const Geom& g);
+OpLaunch op_launch32(const Geom& g);
+OpLaunch op_launch64(const Geom& g);
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
             const T* u, const T* f, T* out, T omega, double* dot_partials);

@@ -36,7 +36,10 @@ struct ModalK {           // structure verified on the host (build_modal_k)
 };
 
 constexpr int kOpTX = 32;
-constexpr int kOpTY = 8;
+// CTA height (32 x 8 threads; measured faster than 32 x 16 for FP32, and
+// the FP64 body needs ~220 registers)
+template <typename T>
+__host__ __device__ constexpr int op_ty() { return 8; }
 
 template <typename T>
 __device__ __forceinline__ void face_forward(const T* c00, const T* c10, const T* c01, const T* c11, T* F) {

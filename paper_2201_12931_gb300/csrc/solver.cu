@@ -21,6 +21,7 @@ struct P;
 template <>
 struct P<double> {
     static const ModalK<double>& mk(topo_grid* h) { return *h->mk64; }
+    static const OpLaunch& op(Level& l) { return l.op64; }
     static const double* E(Level& l) { return l.E64; }
     static VBuf<double>& vb(Level& l) { return l.v64; }
     static const double* W(topo_grid* h) { return h->cs.W64; }
@@ -30,6 +31,7 @@ struct P<double> {
 template <>
 struct P<float> {
     static const ModalK<float>& mk(topo_grid* h) { return *h->mk32; }
+    static const OpLaunch& op(Level& l) { return l.op32; }
     static const float* E(Level& l) { return l.E32; }
     static VBuf<float>& vb(Level& l) { return l.v32; }
     static const float* W(topo_grid* h) { return h->cs.W32; }
@@ -51,7 +53,7 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
         }
         cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
     }
-    const int np = stencil<T>(h->ctx(), mode, lv.op, P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
+    const int np = stencil<T>(h->ctx(), mode, P<T>::op(lv), P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
                               (T)h->prm.omega, dot);
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);

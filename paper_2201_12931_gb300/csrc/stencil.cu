@@ -58,11 +58,11 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // parity B = P & 1, so that double buffers and the two-plane register history
 // are addressed statically (no register moves, no dynamic indexing).
 template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     k_op(const ModalK<T> mk, const T* __restrict__ E, const uint8_t* __restrict__ mask, const T* __restrict__ u,
          const T* __restrict__ f, T* __restrict__ out, const int nx, const int ny, const int nz, const int cz,
          const T omega, double* __restrict__ partials) {
-    constexpr int TX = kOpTX, TY = kOpTY;
+    constexpr int TX = kOpTX, TY = op_ty<T>();
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
     constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
     constexpr bool NEEDF = (MODE != ST_APPLY);
@@ -96,61 +96,78 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
     for (int i = 0; i < 12; ++i) fb[0][i] = fb[1][i] = top[i] = T(0);
     T st00[3] = {}, st10[3] = {}, st01[3] = {}, st11[3] = {};
-    T stE = T(0), Elast = T(0);
-    T hu[2][3] = {}, hf[2][3] = {};
-    unsigned hm[2] = {0u, 0u};
+    T stE = T(0);
     double dot = 0.0;
-    T nu[3] = {}, nf[3] = {}, hv[3] = {}, nE = T(0);
-    unsigned nm = 0u, nhm = 0u;
-    long long ob = (long long)(kz0 - 1) * nplane;    // plane offset of the next fetch
+    // per-plane register slots, slot = plane & 3: own node raw u, f, mask,
+    // the column modulus of the layer below the plane, and (two slots) the
+    // halo node; planes P-2 .. P+1 are live in step P, so no copies occur
+    T su[4][3], sf[4][3], sE[4];
+    unsigned sm[4];
+    T shv[2][3];
+    unsigned shm[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        su[q][0] = su[q][1] = su[q][2] = T(0);
+        sf[q][0] = sf[q][1] = sf[q][2] = T(0);
+        sE[q] = T(0);
+        sm[q] = 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        shv[q][0] = shv[q][1] = shv[q][2] = T(0);
+        shm[q] = 0u;
+    }
+    const int own3 = 3 * own_xy, halo3 = 3 * halo_xy;
 
-    auto fetch = [&](int P) {
+    // load plane P into slot S (plane-uniform base + per-thread offset)
+    auto fetch = [&](auto Sc, int P) {
+        constexpr int S = decltype(Sc)::value;
         const bool pin = P >= 0 && P <= nz;
+        const long long pb = (long long)P * nplane;
         if (NEEDU || NEEDF) {
             const bool ok = pin && node_ok;
-            const long long n = ob + own_xy;
-            nm = ok ? mask[n] : 0u;
+            sm[S] = ok ? mask[pb + own_xy] : 0u;
+            const T* ub = u + 3 * pb + own3;
+            const T* fb_ = f + 3 * pb + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (NEEDU) nu[c] = ok ? u[3 * n + c] : T(0);
-                if (NEEDF) nf[c] = ok ? f[3 * n + c] : T(0);
+                if (NEEDU) su[S][c] = ok ? ub[c] : T(0);
+                if (NEEDF) sf[S][c] = ok ? fb_[c] : T(0);
             }
         }
         if (NEEDU) {
             const bool okh = pin && halo_ok;
-            const long long n = ob + halo_xy;
-            nhm = okh ? mask[n] : 0u;
+            shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
+            const T* hb = u + 3 * pb + halo3;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) hv[c] = okh ? u[3 * n + c] : T(0);
+            for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? hb[c] : T(0);
         }
-        nE = (col_ok && P >= 1 && P <= nz) ? E[(long long)(P - 1) * nx * ny + col_xy] : T(0);
-        ob += nplane;
+        sE[S] = (col_ok && P >= 1 && P <= nz) ? E[(long long)(P - 1) * nx * ny + col_xy] : T(0);
     };
 
+    // step of node plane P, B = P & 3 (static)
     auto step = [&](auto Bc, int P) {
         constexpr int B = decltype(Bc)::value;
-        T* const U = reinterpret_cast<T*>(smem_raw) + B * nU;
-        T* const Cb = reinterpret_cast<T*>(smem_raw) + 2 * nU + B * nC;
-        T* const Eb = reinterpret_cast<T*>(smem_raw) + 2 * nU + 2 * nC + B * nEs;
-        const unsigned cm = nm, chm = nhm;
-        const T cE = nE;
-        T cu[3], cf[3], ch[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cu[c] = nu[c];
-            cf[c] = nf[c];
-            ch[c] = hv[c];
-        }
-        if (P + 1 <= kz1) fetch(P + 1);
+        constexpr int B2 = B & 1;                 // shared-memory buffer
+        constexpr int SN = (B + 1) & 3;           // slot of plane P + 1
+        constexpr int SO = (B + 2) & 3;           // slot of plane P - 2 (output)
+        constexpr int SL = (B + 3) & 3;           // slot of plane P - 1
+        T* const U = reinterpret_cast<T*>(smem_raw) + B2 * nU;
+        T* const Cb = reinterpret_cast<T*>(smem_raw) + 2 * nU + B2 * nC;
+        T* const Eb = reinterpret_cast<T*>(smem_raw) + 2 * nU + 2 * nC + B2 * nEs;
         // publish plane P (masked) and the stashed contributions of plane P - 2
         if (NEEDU) {
-            T mu[3];
+            const unsigned cm = sm[B];
+            T mu[3] = {su[B][0], su[B][1], su[B][2]};
+            if (cm) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) mu[c] = ((cm >> c) & 1u) ? T(0) : cu[c];
+                for (int c = 0; c < 3; ++c) mu[c] = ((cm >> c) & 1u) ? T(0) : su[B][c];
+            }
             st3(U + uoff, mu);
             if (has_halo) {
+                const unsigned chm = shm[B & 1];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) mu[c] = ((chm >> c) & 1u) ? T(0) : ch[c];
+                for (int c = 0; c < 3; ++c) mu[c] = ((chm >> c) & 1u) ? T(0) : shv[B & 1][c];
                 st3(U + hoff, mu);
             }
             st3(Cb + coff, st10);
@@ -158,8 +175,10 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
             st3(Cb + 2 * (nC / 3) + coff, st11);
         }
         if (NEEDD) Eb[ty * TX + tx] = stE;
+        // start loading plane P + 1 (its slot held plane P - 3, no longer needed)
+        if (P + 1 <= kz1) fetch(std::integral_constant<int, SN>{}, P + 1);
         __syncthreads();
-        // output node plane Q = P - 2 (history slot B)
+        // output node plane Q = P - 2
         const int Q = P - 2;
         if (out_ok && Q >= kz0 && Q < kz1) {
             T y[3] = {T(0), T(0), T(0)};
@@ -176,13 +195,13 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
                 const T* e = Eb + ty * TX + tx;
                 rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
-            T* o = out + 3 * ((long long)Q * nplane + own_xy);
-            const unsigned m2 = hm[B];
+            T* o = out + 3 * ((long long)Q * nplane) + own3;
+            const unsigned m2 = sm[SO];
             T d32 = T(0);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const bool fixed = (m2 >> c) & 1u;
-                const T uo = hu[B][c], fo = hf[B][c];
+                const T uo = su[SO][c], fo = sf[SO][c];
                 T r;
                 if (MODE == ST_APPLY) {
                     r = fixed ? uo : y[c];
@@ -209,9 +228,9 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
                 ld3(U + uoff + 4, c10);
                 ld3(U + uoff + (TX + 1) * 4, c01);
                 ld3(U + uoff + (TX + 1) * 4 + 4, c11);
-                face_forward<T>(c00, c10, c01, c11, fb[B]);
+                face_forward<T>(c00, c10, c01, c11, fb[B2]);
                 T Bo[12], To[12];
-                element_modal<T>(mk, cE, fb[B ^ 1], fb[B], Bo, To);
+                element_modal<T>(mk, sE[B], fb[B2 ^ 1], fb[B2], Bo, To);
                 T A[12];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) {
@@ -220,37 +239,37 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
                 }
                 face_inverse<T>(A, st00, st10, st01, st11);
             }
-            if (NEEDD) stE = Elast + cE;
+            if (NEEDD) stE = sE[SL] + sE[B];
         } else if (NEEDU && P == kz0 - 1) {
             T c00[3], c10[3], c01[3], c11[3];
             ld3(U + uoff, c00);
             ld3(U + uoff + 4, c10);
             ld3(U + uoff + (TX + 1) * 4, c01);
             ld3(U + uoff + (TX + 1) * 4 + 4, c11);
-            face_forward<T>(c00, c10, c01, c11, fb[B]);
+            face_forward<T>(c00, c10, c01, c11, fb[B2]);
         }
-        Elast = cE;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            hu[B][c] = cu[c];
-            hf[B][c] = cf[c];
-        }
-        hm[B] = cm;
     };
 
-    using B0 = std::integral_constant<int, 0>;
-    using B1 = std::integral_constant<int, 1>;
-    fetch(kz0 - 1);
-    int P = kz0 - 1;
-    if (P & 1) {
-        step(B1{}, P);
-        ++P;
+    using S0 = std::integral_constant<int, 0>;
+    using S1 = std::integral_constant<int, 1>;
+    using S2 = std::integral_constant<int, 2>;
+    using S3 = std::integral_constant<int, 3>;
+    // planes kz0-1 .. kz1+1 are processed; the range is widened to whole
+    // groups of four (P = 0 mod 4 first) -- the extra steps are guarded no-ops
+    const int Pfirst = kz0 - 1;
+    int P = Pfirst - (((Pfirst % 4) + 4) % 4);
+    switch (Pfirst - P) {   // prefetch plane Pfirst into its slot
+        case 0: fetch(S0{}, Pfirst); break;
+        case 1: fetch(S1{}, Pfirst); break;
+        case 2: fetch(S2{}, Pfirst); break;
+        default: fetch(S3{}, Pfirst); break;
     }
-    for (; P + 1 <= kz1 + 1; P += 2) {
-        step(B0{}, P);
-        step(B1{}, P + 1);
+    for (; P <= kz1 + 1; P += 4) {
+        step(S0{}, P);
+        step(S1{}, P + 1);
+        step(S2{}, P + 2);
+        step(S3{}, P + 3);
     }
-    if (P <= kz1 + 1) step(B0{}, P);
     if (DOT) {
         double v = dot;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -267,7 +286,8 @@ __global__ void __launch_bounds__(kOpTX * kOpTY, sizeof(T) == 4 ? 2 : 1)
 
 template <typename T>
 constexpr size_t op_smem_bytes() {
-    return sizeof(T) * (2 * (kOpTY + 1) * (kOpTX + 1) * 4 + 2 * 3 * kOpTY * kOpTX * 4 + 2 * kOpTY * kOpTX);
+    constexpr int TY = op_ty<T>();
+    return sizeof(T) * (2 * (TY + 1) * (kOpTX + 1) * 4 + 2 * 3 * TY * kOpTX * 4 + 2 * TY * kOpTX);
 }
 
 template <typename T, int MODE, bool DOT>
@@ -278,7 +298,7 @@ void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E,
         cudaFuncSetAttribute(k_op<T, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_smem_bytes<T>());
         attr = true;
     }
-    k_op<T, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, kOpTY), op_smem_bytes<T>(), c.s>>>(
+    k_op<T, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, op_ty<T>()), op_smem_bytes<T>(), c.s>>>(
         mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot);
     TOPO_LAUNCH_CHECK(c);
 }
@@ -384,22 +404,25 @@ __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double*
 
 }  // namespace
 
-OpLaunch op_launch(const Geom& g) {
+OpLaunch op_launch(const Geom& g, int ty, int target_ctas) {
     OpLaunch L;
     L.g = g;
     L.gx = (g.nx + 1 + kOpTX - 2) / (kOpTX - 1);
-    L.gy = (g.ny + 1 + kOpTY - 2) / (kOpTY - 1);
+    L.gy = (g.ny + 1 + ty - 2) / (ty - 1);
     const long long xy = (long long)L.gx * L.gy;
     const int NZ = g.nz + 1;
-    // enough CTAs for ~4 waves of 2 resident CTAs on 152 SMs, but chunks of at
-    // least 16 planes (each chunk recomputes one layer and two exchange steps)
-    const long long gz_target = (1216 + xy - 1) / xy;
+    // enough CTAs for a few waves, but chunks of at least 16 planes (each
+    // chunk recomputes one layer and two exchange steps)
+    const long long gz_target = (target_ctas + xy - 1) / xy;
     int cz = (int)((NZ + gz_target - 1) / gz_target);
     cz = cz < 16 ? (NZ < 16 ? NZ : 16) : cz;
     L.cz = cz;
     L.gz = (NZ + cz - 1) / cz;
     return L;
 }
+
+OpLaunch op_launch32(const Geom& g) { return op_launch(g, op_ty<float>(), 1216); }
+OpLaunch op_launch64(const Geom& g) { return op_launch(g, op_ty<double>(), 608); }
 
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,

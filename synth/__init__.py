@@ -43,6 +43,18 @@ def uniform01(seed: int, count: int, start: int = 0) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
+def uniform01_at(seed: int, idx) -> np.ndarray:
+    """Draws number idx (any array of indices) of stream `seed`: the same
+    values uniform01(seed, n)[idx] gives, without generating the others."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (idx + np.uint64(1)) * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
 def uniform_field(dims, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
     """Per-element field U[lo, hi) in element order (x fastest), float64."""
     nx, ny, nz = dims
@@ -93,6 +105,13 @@ class Problem:
     f: np.ndarray              # float64, 3*nodes
     name: str = ""
     info: dict = field(default_factory=dict)
+
+
+def cantilever_fixed_at(dims, dofs) -> np.ndarray:
+    """Dirichlet flags of the cantilever (face x = 0 clamped) at given DOFs."""
+    nx, _, _ = dims
+    node = np.asarray(dofs) // 3
+    return (node % (nx + 1) == 0).astype(np.uint8)
 
 
 def cantilever(dims) -> Problem:

@@ -41,3 +41,15 @@ def test_mbb_constraints():
 def test_sample_without_replacement():
     s = synth.sample_without_replacement(2, 1000, 64)
     assert len(set(s.tolist())) == 64 and s.min() >= 0 and s.max() < 1000
+
+
+def test_uniform01_at_matches_stream():
+    idx = np.array([0, 5, 99, 12345, 7])
+    assert np.array_equal(synth.uniform01_at(9, idx), synth.uniform01(9, 20000)[idx])
+
+
+def test_cantilever_fixed_at_matches_mask():
+    dims = (5, 3, 2)
+    pb = synth.cantilever(dims)
+    dofs = np.arange(pb.fixed.size)
+    assert np.array_equal(synth.cantilever_fixed_at(dims, dofs), pb.fixed)
