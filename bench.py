@@ -48,6 +48,8 @@ def parse_args(argv=None):
                     help="relative residual of the timed all-FP64 comparison solve")
     ap.add_argument("--fp64-ref", choices=["full", "skip"], default="full")
     ap.add_argument("--cpu-baseline", choices=["on", "off"], default="on")
+    ap.add_argument("--oc-loop", action="store_true",
+                    help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -240,14 +242,45 @@ def kernel_table(grid, nn, ne):
     return rows, peak, src
 
 
-def roofline(rows, peak, src):
+KERNEL_SOURCES = ["paper_2201_12931_gb300/csrc/stencil.cu", "paper_2201_12931_gb300/csrc/operator.cuh"]
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(mode, prec, ne):
+    """DRAM bytes per launch of an operator kernel from profiles/traffic.json,
+    scaled to `ne` elements; None if absent or taken on other kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    if t.get("kernel_sha256") != kernel_hash():
+        return None
+    for e in t.get("entries", []):
+        if e["mode"] == mode and e["prec"] == prec:
+            d = e["dims"]
+            return (e["dram_bytes_read"] + e["dram_bytes_write"]) * ne / (d[0] * d[1] * d[2])
+    return None
+
+
+def roofline(rows, peak, src, ne):
     """Dominant fine-level operator kernel (largest total time) from the live event records."""
     if not rows:
         return None
     r = max(rows, key=lambda v: v["total_ms"])
+    tr = measured_traffic(r["mode"], r["prec"], ne)
     return {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": r["frac"],
-            "traffic": None, "kernel": r["kernel"], "launches": r["launches"], "avg_launch_ms": r["avg_launch_ms"],
-            "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"], "peak_source": src}
+            "traffic": None if tr is None else int(tr), "kernel": r["kernel"], "launches": r["launches"],
+            "avg_launch_ms": r["avg_launch_ms"], "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"],
+            "peak_source": src}
 
 
 def run_ours(args):
@@ -324,7 +357,7 @@ def run_ours(args):
     solve_s = [a.elapsed_time(b) / 1e3 for a, b, _, _, _, _ in rec]
     step_s = [a.elapsed_time(c) / 1e3 for a, _, c, _, _, _ in rec]
     rows, peak, src = kernel_table(g, nn, ne)
-    roof = roofline(rows, peak, src)
+    roof = roofline(rows, peak, src, ne)
     res_last, C_mixed = rec[-1][3], rec[-1][4]
     t_solve = statistics.mean(solve_s)
     t_step = statistics.mean(step_s)
@@ -407,6 +440,62 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_oc_loop(args):
+    """Algorithm 4 with the density filter for the workload's iteration count,
+    once with the workload's precision and once all-FP64 (warm-started solves,
+    rel. residual from the workload); prints one JSON line with the time per
+    iteration of both and the compliance drift of the first against the second."""
+    import torch
+    import synth
+    from paper_2201_12931_gb300 import Params, TopoGrid, TOPO_FP64, TOPO_MIXED, TOPO_MIXED_BF16
+    name = args.workload if "oc" in synth.WORKLOADS[args.workload] else "cantilever_256x128x128_oc50"
+    w = synth.WORKLOADS[name]
+    dims = tuple(int(v) for v in args.dims.split("x")) if args.dims else tuple(w["dims"])
+    levels = args.levels or w["levels"]
+    while levels > 1 and any(d % (1 << (levels - 1)) for d in dims):
+        levels -= 1
+    oc = w["oc"]
+    dev = torch.device("cuda", 0)
+    pb = synth.make_problem(name, dims)
+    fixed_d, f_d = torch.tensor(pb.fixed, device=dev), torch.tensor(pb.f, device=dev)
+    ne = dims[0] * dims[1] * dims[2]
+    x0 = torch.tensor(synth.raw_density(name, dims), device=dev)
+    prec = {"fp64": TOPO_FP64, "mixed": TOPO_MIXED, "mixed_bf16": TOPO_MIXED_BF16}[w["precision"]]
+    tol = w.get("rel_tol", 1e-8)
+    out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
+           "iterations": oc["iters"], "rel_tol": tol, "rmin": oc["rmin"], "move": oc["move"],
+           "volfrac": oc["volfrac"]}
+    runs = {}
+    for label, p in (("mixed", prec), ("fp64", TOPO_FP64)):
+        g = TopoGrid(dims, Params(levels=levels, precision=p))
+        g.set_bc_loads(fixed_d, f_d)
+        x = x0.clone()
+        dc = torch.empty(ne, dtype=torch.float64, device=dev)
+        Cs, its, ms = [], [], []
+        for it in range(oc["iters"]):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.set_density(g.filter(oc["rmin"], x))
+            _, res = g.solve(tol, 20000)
+            C, _ = g.compliance_and_sensitivity(dc)
+            g.oc_update(oc["rmin"], oc["move"], oc["volfrac"], x, dc)
+            e1.record()
+            torch.cuda.synchronize()
+            Cs.append(C)
+            its.append(res.iters)
+            ms.append(e0.elapsed_time(e1))
+        g.close()
+        runs[label] = dict(C=Cs, iters=its, ms=ms)
+        out[label] = {"ms_per_iteration": round(statistics.mean(ms), 3), "total_s": round(sum(ms) / 1e3, 3),
+                      "pcg_iterations": its, "compliance_first": Cs[0], "compliance_last": Cs[-1],
+                      "precision": label if label == "fp64" else w["precision"]}
+    drift = [abs(a - b) / abs(b) for a, b in zip(runs["mixed"]["C"], runs["fp64"]["C"])]
+    out["compliance_drift_max"] = max(drift)
+    out["compliance_drift_last"] = drift[-1]
+    out["compliance_drift"] = [float(f"{d:.3e}") for d in drift]
+    print(json.dumps(out))
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -430,6 +519,8 @@ def main():
     args = parse_args()
     if args.cpu_child:
         run_cpu_child(args)
+    elif args.oc_loop:
+        run_oc_loop(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
