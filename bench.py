@@ -48,6 +48,8 @@ def parse_args(argv=None):
                     help="relative residual of the timed all-FP64 comparison solve")
     ap.add_argument("--fp64-ref", choices=["full", "skip"], default="full")
     ap.add_argument("--cpu-baseline", choices=["on", "off"], default="on")
+    ap.add_argument("--coarsening", choices=["density", "modulus"], default="density",
+                    help="coarse moduli from the mean child density (Sec. 4.2.2) or the mean child modulus")
     ap.add_argument("--oc-loop", action="store_true",
                     help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
@@ -309,7 +311,8 @@ def run_ours(args):
     rmin = w.get("oc", {}).get("rmin", w["density"].get("rmin", 1.5))
     move = w.get("oc", {}).get("move", 0.2)
 
-    g = TopoGrid(dims, Params(levels=levels, precision=prec))
+    hom = 1 if args.coarsening == "modulus" else 0
+    g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom))
     rho0 = physical_density(g, args.workload, dims, dev)
     volfrac = w.get("oc", {}).get("volfrac", float(rho0.mean()))
     g.set_bc_loads(fixed_d, f_d)
@@ -396,7 +399,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": args.workload if not args.dims else f"{args.workload}@{nx}x{ny}x{nz}",
                    "grid": f"{nx}x{ny}x{nz}", "elements": ne, "dofs": 3 * nn, "levels": levels,
-                   "rel_tol": args.rel_tol, "precision": w["precision"],
+                   "rel_tol": args.rel_tol, "precision": w["precision"], "coarsening": args.coarsening,
                    "l2": "inputs larger than L2 (fine-level vectors >= 129 MB)" if 12 * nn > 129e6
                    else "inputs smaller than L2 (no flush)"},
         "solve": {"status": res_last.status, "inner_iters": res_last.iters, "outer_steps": res_last.outer_steps,
@@ -411,7 +414,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if args.fp64_ref == "full" and prec != TOPO_FP64:
-        g64 = TopoGrid(dims, Params(levels=levels, precision=TOPO_FP64))
+        g64 = TopoGrid(dims, Params(levels=levels, precision=TOPO_FP64, homogenize=hom))
         g64.set_bc_loads(fixed_d, f_d)
         g64.set_density(rho0)
         torch.cuda.synchronize()
@@ -464,10 +467,10 @@ def run_oc_loop(args):
     tol = w.get("rel_tol", 1e-8)
     out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
            "iterations": oc["iters"], "rel_tol": tol, "rmin": oc["rmin"], "move": oc["move"],
-           "volfrac": oc["volfrac"]}
+           "volfrac": oc["volfrac"], "coarsening": args.coarsening}
     runs = {}
     for label, p in (("mixed", prec), ("fp64", TOPO_FP64)):
-        g = TopoGrid(dims, Params(levels=levels, precision=p))
+        g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=1 if args.coarsening == "modulus" else 0))
         g.set_bc_loads(fixed_d, f_d)
         x = x0.clone()
         dc = torch.empty(ne, dtype=torch.float64, device=dev)

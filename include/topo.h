@@ -66,9 +66,13 @@ typedef struct {
     int pre, post;      /* Jacobi sweeps before / after the coarse correction (2,2) */
     double omega;       /* Jacobi damping (0.35); must be < 2/5.318 for an SPD V-cycle */
     int precision;      /* topo_precision (TOPO_FP64)                               */
-    double inner_tol;   /* residual reduction asked of each inner FP32 solve (1e-4) */
+    double inner_tol;   /* residual reduction asked of each inner FP32 solve (1e-4);  */
+                        /* the last one asks only for twice what is still missing */
     int inner_max_it;   /* iteration cap of each inner solve (500)                 */
     int max_refine;     /* cap on outer refinement steps (12)                      */
+    int homogenize;     /* coarse modulus rule (Sec. 4.2.2): 0 = SIMP of the mean   */
+                        /* of the 8 children's densities (the paper's rule,       */
+                        /* default); 1 = mean of the children's moduli            */
 } topo_params;
 
 /* Fills *p with the defaults listed above.  TOPO_BADARG if p is NULL. */

@@ -111,17 +111,22 @@ class Level:
     E: np.ndarray | None = None
 
 
-def homogenized_hierarchy(dims, rho, fixed, K0, levels, E0=1.0, Emin=1e-9, penal=3.0):
-    """Levels 0..levels-1 with on-the-fly style (rediscretised) operators."""
+def homogenized_hierarchy(dims, rho, fixed, K0, levels, E0=1.0, Emin=1e-9, penal=3.0, rule="density"):
+    """Levels 0..levels-1 with rediscretised coarse operators.  rule="density"
+    (the paper's): coarse E = SIMP(mean of the children's densities);
+    rule="modulus" (a variant): coarse E = mean of the children's E."""
     out = []
     d, r, fx = tuple(dims), np.asarray(rho, dtype=np.float64), np.asarray(fixed, dtype=np.uint8)
+    E = simp_modulus(r, E0, Emin, penal)
     for l in range(levels):
-        E = simp_modulus(r, E0, Emin, penal)
+        if rule == "density" or l == 0:
+            E = simp_modulus(r, E0, Emin, penal)
         K = apply_dirichlet(assemble(d, E, (2.0 ** l) * K0), fx)
         out.append(Level(d, K, 1.0 / K.diagonal(), fx, None, r, E))
         if l + 1 < levels:
             fxc = inject_fixed(d, fx)
             out[-1].P = transfer(d, fx, fxc)
+            E = homogenize_density(E, d)
             r = homogenize_density(r, d)
             d = coarse_dims(d)
             fx = fxc

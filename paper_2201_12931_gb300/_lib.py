@@ -22,7 +22,7 @@ class TopoParams(C.Structure):
     _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double), ("penal", C.c_double),
                 ("levels", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("inner_max_it", C.c_int),
-                ("max_refine", C.c_int)]
+                ("max_refine", C.c_int), ("homogenize", C.c_int)]
 
 
 class TopoSolveStats(C.Structure):

@@ -35,6 +35,7 @@ class Params:
     inner_tol: float = 1e-4
     inner_max_it: int = 500
     max_refine: int = 12
+    homogenize: int = 0
 
     def to_c(self) -> L.TopoParams:
         p = L.TopoParams()

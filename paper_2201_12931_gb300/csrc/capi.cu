@@ -301,6 +301,7 @@ topo_status topo_default_params(topo_params* p) {
     p->inner_tol = 1e-4;
     p->inner_max_it = 500;
     p->max_refine = 12;
+    p->homogenize = 0;
     return TOPO_OK;
 }
 
@@ -322,6 +323,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     if (p.precision < TOPO_FP64 || p.precision > TOPO_MIXED_BF16) return fail(nullptr, TOPO_BADARG, "bad precision");
     if (!(p.inner_tol > 0.0 && p.inner_tol < 1.0) || p.inner_max_it < 1 || p.max_refine < 1)
         return fail(nullptr, TOPO_BADARG, "bad inner solver parameters");
+    if (p.homogenize != 0 && p.homogenize != 1) return fail(nullptr, TOPO_BADARG, "homogenize must be 0 or 1");
     if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))
         return fail(nullptr, TOPO_BADARG, "grid too large");
 
@@ -438,8 +440,17 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
     CK(h, cudaMemcpyAsync(h->lev[0].rho, rho_dev, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToDevice, h->stream));
     for (int l = 0; l < h->L; ++l) {
         Level& lv = h->lev[l];
-        simp_moduli(c, lv.g.ne, lv.rho, lv.scale, h->prm.E0, h->prm.Emin, h->prm.penal, lv.E64, lv.E32, h->dflag);
-        if (l + 1 < h->L) homogenize(c, lv.g, lv.rho, h->lev[l + 1].rho);
+        if (l == 0 || h->prm.homogenize == 0)
+            simp_moduli(c, lv.g.ne, lv.rho, lv.scale, h->prm.E0, h->prm.Emin, h->prm.penal, lv.E64, lv.E32,
+                        h->dflag);
+        if (l + 1 < h->L) {
+            Level& lc = h->lev[l + 1];
+            homogenize(c, lv.g, lv.rho, lc.rho, 1.0);
+            if (h->prm.homogenize == 1) {   // E_{l+1} = 2 * mean of the children's E_l
+                homogenize(c, lv.g, lv.E64, lc.E64, 2.0);
+                convert<double, float>(c, lc.g.ne, lc.E64, lc.E32);
+            }
+        }
     }
     CK(h, cudaGetLastError());
     h->have_density = true;

@@ -151,7 +151,8 @@ void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const
 template <typename T>
 void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc,
                  const T* ec, T* uf);
-void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c);
+// coarse = scale * mean of the 8 children (densities: scale 1; moduli: scale 2)
+void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale);
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0,
                  double Emin, double penal, double* E64, float* E32, int* bad_flag);
 void mask_from_dofs(const Ctx& c, long long nn, const uint8_t* fixed_dofs, uint8_t* mask);

@@ -213,7 +213,10 @@ int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres
         const double rr32 = h->host_sc[3];
         int st;
         double rr_in;
-        const double red = h->prm.inner_tol;
+        // inner reduction: inner_tol, loosened on the last step to what is
+        // still missing (with a factor 2 margin) so that it does not overshoot
+        const double missing = tol / std::sqrt(rr / ff);
+        const double red = std::fmin(0.5, std::fmax(h->prm.inner_tol, 0.5 * missing));
         const double target = red * red * rr32;
         const int it = pcg_core<float>(h, h->d32, h->r32, h->z32, h->p32, h->q32, rr32, target,
                                        max_it - total, &st, &rr_in);

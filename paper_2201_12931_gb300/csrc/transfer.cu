@@ -4,7 +4,7 @@
 //                1 at coincident and 1/2 at midpoint nodes)
 //   prolongation u_f += diag(free_f) P diag(free_c) e_c  (Algorithm 3,
 //                "Prolongation correction")
-//   homogenization: coarse density = mean of the 8 children (Sec. 4.2.2)
+//   homogenization: coarse density (or modulus) = mean of the 8 children (Sec. 4.2.2)
 //   SIMP moduli E_l = 2^l (Emin + rho^p (E0 - Emin)) (Eq. K_mod)
 #include "common.cuh"
 
@@ -92,7 +92,7 @@ __global__ void k_prolong_add(const uint8_t* __restrict__ maskf, const uint8_t* 
 }
 
 __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__ rc, int nxf, int nyf,
-                             int nzf) {
+                             int nzf, double scale) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
     const long long nec = (long long)nxc * nyc * nzc;
     const long long E = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -106,7 +106,7 @@ __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__
         const long long e = (2 * I + (c & 1)) + (long long)nxf * ((2 * J + ((c >> 1) & 1)) + (long long)nyf * (2 * K + (c >> 2)));
         s += rf[e];
     }
-    rc[E] = 0.125 * s;
+    rc[E] = (0.125 * scale) * s;
 }
 
 // rho^p: repeated multiplication for integer p (FP64 pow is slow on this part)
@@ -179,9 +179,9 @@ template void prolong_add<double>(const Ctx&, const Geom&, const uint8_t*, const
                                   double*);
 template void prolong_add<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, float*);
 
-void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c) {
+void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale) {
     const long long nec = (long long)(gf.nx / 2) * (gf.ny / 2) * (gf.nz / 2);
-    k_homogenize<<<grid_for(nec, 256), 256, 0, c.s>>>(rho_f, rho_c, gf.nx, gf.ny, gf.nz);
+    k_homogenize<<<grid_for(nec, 256), 256, 0, c.s>>>(rho_f, rho_c, gf.nx, gf.ny, gf.nz, scale);
     TOPO_LAUNCH_CHECK(c);
 }
 

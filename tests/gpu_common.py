@@ -25,8 +25,9 @@ def make_case(dims, levels, problem="cantilever", seed=3, lo=1e-3, hi=1.0, preci
     g.set_density(torch.tensor(rho, device=dev))
     g.set_bc_loads(torch.tensor(pb.fixed, device=dev), torch.tensor(pb.f, device=dev))
     K0 = element.element_stiffness(g.params.nu)
+    rule = "modulus" if g.params.homogenize == 1 else "density"
     H = multigrid.homogenized_hierarchy(dims, rho, pb.fixed, K0, levels, g.params.E0, g.params.Emin,
-                                        g.params.penal)
+                                        g.params.penal, rule=rule)
     return g, pb, rho, H
 
 

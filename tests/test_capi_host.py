@@ -41,6 +41,7 @@ def test_default_params(lib):
     p = TopoParams()
     assert lib.topo_default_params(C.byref(p)) == 0
     assert (p.E0, p.Emin, p.nu, p.penal, p.omega, p.pre, p.post) == (1.0, 1e-9, 0.3, 3.0, 0.35, 2, 2)
+    assert p.homogenize == 0
     assert lib.topo_default_params(None) == 1
 
 
@@ -73,6 +74,11 @@ def test_create_grid_rejects_bad_omega_and_nu(lib):
     p.levels = 1
     p.nu = 0.5
     assert lib.topo_create_grid(2, 2, 2, C.byref(p), None, C.byref(h)) == 1
+    lib.topo_default_params(C.byref(p))
+    p.levels = 1
+    p.homogenize = 2
+    assert lib.topo_create_grid(2, 2, 2, C.byref(p), None, C.byref(h)) == 1
+    assert "homogenize" in lib.topo_last_error(None).decode()
 
 
 def test_null_handle_calls_are_rejected(lib):

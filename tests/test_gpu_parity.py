@@ -72,6 +72,23 @@ def test_vcycle(dims, levels, precision, tol):
     assert rel_max(z, ref) < tol, rel_max(z, ref)
 
 
+@pytest.mark.parametrize("dims,levels", [((48, 24, 24), 3), ((40, 24, 16), 4)])
+def test_modulus_averaging_variant(dims, levels):
+    """Coarse moduli = mean of the children's moduli (homogenize = 1): the
+    operators of every level and the V-cycle against the oracle's hierarchy
+    built with the same rule."""
+    g, pb, rho, H = make_case(dims, levels, seed=6, lo=0.0, hi=1.0, homogenize=1)
+    for l in range(levels):
+        nl = H[l].K.shape[0]
+        u = synth.uniform_field((nl, 1, 1), 200 + l, -1.0, 1.0)
+        assert rel_max(n(g.apply_operator(t(u), level=l, precision=0)), H[l].K @ u) < 1e-12
+        assert rel_max(n(g.apply_operator(t(u), level=l, precision=1)), H[l].K @ u) < 1e-5
+    r = synth.uniform_field((H[0].K.shape[0], 1, 1), 13, -1, 1)
+    r[pb.fixed.astype(bool)] = 0.0
+    ref = multigrid.vcycle(H, r, g.params.omega, g.params.pre, g.params.post)
+    assert rel_max(n(g.vcycle(t(r), precision=0)), ref) < 1e-10
+
+
 @pytest.mark.parametrize("r", [1.5, 2.0, 2.5, 3.0])
 @pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 9)])
 def test_filter_and_transpose(r, dims):

@@ -94,6 +94,46 @@ def test_homogenized_operator_is_not_galerkin_for_varying_density():
     assert np.abs(Kg - H[1].K.toarray()).max() > 1e-3 * np.abs(Kg).max()
 
 
+def _linear_field(dims, A, h=1.0):
+    """Nodal values of u(x) = A x on a grid of element size h (node-major)."""
+    nx, ny, nz = dims
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    X = h * np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
+    return (X @ A.T).reshape(-1)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_modulus_rule_reproduces_linear_field_energy(levels):
+    """Averaging the moduli gives each coarse element the energy its 8^l fine
+    descendants store under any uniform strain (a linear displacement field
+    has the same strain in every child), so u_c^T K_c u_c = u_f^T K_h u_f.
+    Averaging the densities instead stores less (Jensen: mean(rho)^3 <=
+    mean(rho^3)).  Pins the modulus averaging, the 2^l element scaling and
+    their chaining over levels."""
+    dims = (8, 8, 4)
+    rho = synth.uniform_field(dims, 21, 0.0, 1.0)
+    free = np.zeros(3 * grid.n_nodes(dims), dtype=np.uint8)
+    A = synth.uniform_field((3, 3, 1), 22, -1.0, 1.0).reshape(3, 3)
+    Hm = multigrid.homogenized_hierarchy(dims, rho, free, K0, levels, rule="modulus")
+    Hd = multigrid.homogenized_hierarchy(dims, rho, free, K0, levels, rule="density")
+    uf = _linear_field(dims, A)
+    ef = uf @ (Hm[0].K @ uf)
+    for l in range(1, levels):
+        uc = _linear_field(Hm[l].dims, A, h=2.0 ** l)
+        assert uc @ (Hm[l].K @ uc) == pytest.approx(ef, rel=1e-12)
+        assert uc @ (Hd[l].K @ uc) < 0.9 * ef
+
+
+def test_modulus_rule_equals_density_rule_for_uniform_density():
+    dims = (8, 4, 4)
+    pb = synth.cantilever(dims)
+    rho = np.full(grid.n_elems(dims), 0.37)
+    Hm = multigrid.homogenized_hierarchy(dims, rho, pb.fixed, K0, 3, rule="modulus")
+    Hd = multigrid.homogenized_hierarchy(dims, rho, pb.fixed, K0, 3, rule="density")
+    for a, b in zip(Hm, Hd):
+        assert np.abs((a.K - b.K).toarray()).max() < 1e-14 * np.abs(b.K.toarray()).max()
+
+
 def _vcycle_matrix(H, **kw):
     n = H[0].K.shape[0]
     M = np.zeros((n, n))
