@@ -221,6 +221,9 @@ def op_bytes(mode, prec, nn, ne):
     """Algorithmic HBM bytes of one fine-level operator launch: the nodal
     vectors it must read and write (3 DOFs per node) plus one modulus per
     element; s = 8 (FP64 kernel) or 4 (FP32 kernel)."""
+    if prec == 2:   # BF16 iterates u (in) and u' (out, FP32 for the last sweep), FP32 f and residual
+        su, sf, so = 2, 4, 2
+        return 3 * nn * ({0: su + so, 1: su + sf + so, 2: su + sf + 4, 3: sf + so}[mode]) + ne * 4
     s = 8 if prec == 0 else 4
     nvec = {0: 2, 1: 3, 2: 3, 3: 2}[mode]   # K.u: u, y | Jacobi: u, f, u' | residual: u, f, r | first: f, u'
     return nvec * 3 * nn * s + ne * s
@@ -231,13 +234,13 @@ def kernel_table(grid, nn, ne):
     rows = []
     for mode in range(4):
         cnt, ms = grid.profile_read(mode)
-        for prec in (0, 1):
+        for prec in (0, 1, 2):
             if not cnt[prec]:
                 continue
             b = op_bytes(mode, prec, nn, ne)
             avg = ms[prec] / cnt[prec]
             gbs = b / (avg / 1e3) / 1e9
-            rows.append({"kernel": f"{OP_NAMES[mode]} ({'fp64' if prec == 0 else 'fp32'}) fine level",
+            rows.append({"kernel": f"{OP_NAMES[mode]} ({('fp64', 'fp32', 'fp32, bf16 iterates')[prec]}) fine level",
                          "mode": mode, "prec": prec, "launches": cnt[prec], "total_ms": round(ms[prec], 3),
                          "avg_launch_ms": round(avg, 4), "algorithmic_bytes_per_launch": b,
                          "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})

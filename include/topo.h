@@ -53,7 +53,8 @@ typedef enum {
 typedef enum {
     TOPO_FP64 = 0,       /* all vectors and arithmetic in FP64                */
     TOPO_MIXED = 1,      /* FP32 inner MGPCG inside FP64 iterative refinement */
-    TOPO_MIXED_BF16 = 2  /* as TOPO_MIXED, V-cycle iterates stored in BF16    */
+    TOPO_MIXED_BF16 = 2  /* as TOPO_MIXED, V-cycle iterates stored in BF16 on */
+                         /* all levels above the coarsest (FP32 arithmetic)  */
 } topo_precision;
 
 /* Solver and material parameters.  Defaults from topo_default_params. */
@@ -192,7 +193,11 @@ topo_status topo_prolong_add(topo_handle h, int level, const double* coarse_dev,
 topo_status topo_level_density(topo_handle h, int level, double* rho_dev_out);
 
 /* One V-cycle z = M^-1 r from z = 0 (Algorithm 3, the preconditioner of
- * Algorithm 1), with the direct coarsest solve. */
+ * Algorithm 1), with the direct coarsest solve.  precision: TOPO_FP64,
+ * TOPO_MIXED (FP32 vectors and arithmetic) or TOPO_MIXED_BF16 (FP32
+ * arithmetic, FP32 right-hand sides and residuals, smoother iterates and
+ * prolongated corrections stored in BF16 on every level above the coarsest;
+ * the level-0 result is FP32).  r and z: device FP64, 3*nodes each. */
 topo_status topo_vcycle(topo_handle h, int precision, const double* r_dev, double* z_dev);
 
 /* Statistics of the last topo_solve_state. */
@@ -222,7 +227,8 @@ topo_status topo_profile_enable(topo_handle h, int on);
 /* Synchronises the stream and returns, for operator kind `mode` (0 = K.u,
  * 1 = Jacobi sweep, 2 = residual, 3 = first sweep from zero), the number of
  * recorded launches and their summed device time in milliseconds, split by
- * precision: index 0 = FP64 kernel, 1 = FP32 kernel (arrays of length 2). */
+ * kernel precision: index 0 = FP64, 1 = FP32, 2 = FP32 arithmetic with BF16
+ * iterates (V-cycle of TOPO_MIXED_BF16) -- arrays of length 3. */
 topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms);
 
 /* Density filter for callers that cannot allocate GPU memory (no counterpart

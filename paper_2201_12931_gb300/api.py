@@ -210,11 +210,12 @@ class TopoGrid:
         self._check(self.lib.topo_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self, mode: int):
-        """(launches, total_ms) per precision [fp64, fp32] for operator kind `mode`."""
-        n = (C.c_longlong * 2)()
-        ms = (C.c_double * 2)()
+        """(launches, total_ms) per kernel precision [fp64, fp32, fp32 with BF16
+        iterates] for operator kind `mode`."""
+        n = (C.c_longlong * 3)()
+        ms = (C.c_double * 3)()
         self._check(self.lib.topo_profile_read(self._h, mode, n, ms))
-        return [n[0], n[1]], [ms[0], ms[1]]
+        return list(n), list(ms)
 
     def launch_count(self) -> int:
         v = C.c_longlong(0)

@@ -81,10 +81,21 @@ __global__ void __launch_bounds__(1024) k_cg_beta(const double* __restrict__ p, 
     const double rz = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
         const double old = sc->rz;
+        sc->rz_old = old;
         sc->rz_new = rz;
         sc->beta = (old != 0.0 && isfinite(rz)) ? rz / old : 0.0;
         if (!isfinite(rz)) sc->aux = 1.0;
         sc->rz = rz;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_cg_beta_flexible(const double* __restrict__ p, int n, Scalars* sc) {
+    __shared__ double sh[32];
+    const double zq = sum_partials(p, n, sh);
+    if (threadIdx.x == 0) {
+        const double old = sc->rz_old;
+        sc->beta = (old != 0.0 && isfinite(zq)) ? -sc->alpha * zq / old : 0.0;
+        if (!isfinite(zq)) sc->aux = 1.0;
     }
 }
 
@@ -285,6 +296,10 @@ void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc) {
     k_cg_beta<<<1, 1024, 0, c.s>>>(partials, n, sc);
     TOPO_LAUNCH_CHECK(c);
 }
+void cg_beta_flexible(const Ctx& c, const double* partials, int n, Scalars* sc) {
+    k_cg_beta_flexible<<<1, 1024, 0, c.s>>>(partials, n, sc);
+    TOPO_LAUNCH_CHECK(c);
+}
 
 template <typename T>
 void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, const T* q, T* x, T* r,
@@ -312,6 +327,7 @@ void convert(const Ctx& c, long long n, const S* src, D* dst) {
 }
 template void convert<double, float>(const Ctx&, long long, const double*, float*);
 template void convert<float, double>(const Ctx&, long long, const float*, double*);
+template void convert<bf16, float>(const Ctx&, long long, const bf16*, float*);
 
 void axpy_f32_into_f64(const Ctx& c, long long n, const float* d, double* x) {
     k_axpy_f32<<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, d, x);

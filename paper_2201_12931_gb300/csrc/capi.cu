@@ -139,6 +139,18 @@ topo_status alloc_precision(topo_grid* h, bool fp64) {
     return TOPO_OK;
 }
 
+// BF16 V-cycle iterates on levels 0 .. L-2 (TOPO_MIXED_BF16)
+topo_status alloc_bf16(topo_grid* h) {
+    if (h->bf16_ready) return TOPO_OK;
+    for (int l = 0; l + 1 < h->L; ++l) {
+        const long long n = 3 * h->lev[l].g.nn;
+        ALLOC(h, h->lev[l].ha, n);
+        ALLOC(h, h->lev[l].hb, n);
+    }
+    h->bf16_ready = true;
+    return TOPO_OK;
+}
+
 void free_all(topo_grid* h) {
     auto F = [](void* p) {
         if (p) cudaFree(p);
@@ -147,6 +159,7 @@ void free_all(topo_grid* h) {
         F(l.rho); F(l.E64); F(l.E32); F(l.mask);
         F(l.v64.a); F(l.v64.b); F(l.v64.f);
         F(l.v32.a); F(l.v32.b); F(l.v32.f);
+        F(l.ha); F(l.hb);
     }
     F(h->cs.A); F(h->cs.W64); F(h->cs.WT64); F(h->cs.W32); F(h->cs.WT32); F(h->cs.y64); F(h->cs.y32);
     F(h->cs.info);
@@ -395,6 +408,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     h->cs.n = (int)std::min<long long>(3 * h->lev[h->L - 1].g.nn, 1LL << 30);
     h->cs.npad = (h->cs.n + 31) / 32 * 32;
     TRY(alloc_precision(h, p.precision == TOPO_FP64));
+    if (p.precision == TOPO_MIXED_BF16) TRY(alloc_bf16(h));
     if (cudaMallocHost((void**)&h->host_sc, sizeof(Scalars)) != cudaSuccess) {
         h->host_sc = nullptr;
         h->err = "cudaMallocHost failed";
@@ -607,11 +621,17 @@ topo_status topo_level_dims(topo_handle h, int level, int* nx, int* ny, int* nz)
     return TOPO_OK;
 }
 
-static topo_status step_check(topo_grid* h, int level, int precision) {
+static topo_status step_check(topo_grid* h, int level, int precision, bool allow_bf16 = false) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
     if (level < 0 || level >= h->L) return fail(h, TOPO_BADARG, "level out of range");
-    if (precision != TOPO_FP64 && precision != TOPO_MIXED) return fail(h, TOPO_BADARG, "precision must be 0 or 1");
+    if (precision == TOPO_MIXED_BF16 && allow_bf16) {
+        if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
+        s = alloc_precision(h, false);
+        return s != TOPO_OK ? s : alloc_bf16(h);
+    }
+    if (precision != TOPO_FP64 && precision != TOPO_MIXED)
+        return fail(h, TOPO_BADARG, allow_bf16 ? "precision must be 0, 1 or 2" : "precision must be 0 or 1");
     if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
     return alloc_precision(h, precision == TOPO_FP64);
 }
@@ -680,7 +700,7 @@ topo_status topo_level_density(topo_handle h, int level, double* rho_dev_out) {
 }
 
 topo_status topo_vcycle(topo_handle h, int precision, const double* r_dev, double* z_dev) {
-    topo_status s = step_check(h, 0, precision);
+    topo_status s = step_check(h, 0, precision, true);
     if (s != TOPO_OK) return s;
     if (!r_dev || !z_dev || r_dev == z_dev) return fail(h, TOPO_BADARG, "bad pointers");
     s = ensure_coarse(h);
@@ -689,6 +709,11 @@ topo_status topo_vcycle(topo_handle h, int precision, const double* r_dev, doubl
     const long long n = 3 * l0.g.nn;
     if (precision == TOPO_FP64) {
         vcycle<double>(h, 0, r_dev, z_dev, l0.v64.a, nullptr);
+    } else if (precision == TOPO_MIXED_BF16) {
+        const Ctx c = h->ctx();
+        convert<double, float>(c, n, r_dev, l0.v32.f);
+        vcycle_bf16(h, 0, l0.v32.f, l0.v32.b, nullptr);
+        convert<float, double>(c, n, l0.v32.b, z_dev);
     } else {
         const Ctx c = h->ctx();
         convert<double, float>(c, n, r_dev, l0.v32.f);
@@ -736,15 +761,17 @@ topo_status topo_profile_read(topo_handle h, int mode, long long* launches, doub
     if (s != TOPO_OK) return s;
     if (mode < 0 || mode > 3 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
     CK(h, cudaStreamSynchronize(h->stream));
-    launches[0] = launches[1] = 0;
-    total_ms[0] = total_ms[1] = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        launches[q] = 0;
+        total_ms[q] = 0.0;
+    }
     for (int i = 0; i < h->prof_n; ++i) {
-        const int k = h->prof_kind[i];
-        if (k / 2 != mode) continue;
+        const int k = h->prof_kind[i];   // mode * 4 + precision slot
+        if (k / 4 != mode) continue;
         float ms = 0.f;
         CK(h, cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
-        launches[k & 1] += 1;
-        total_ms[k & 1] += ms;
+        launches[k & 3] += 1;
+        total_ms[k & 3] += ms;
     }
     return TOPO_OK;
 }

@@ -8,6 +8,7 @@
 //                    V-cycle work vectors of each precision.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +19,8 @@
 #include "topo.h"
 
 namespace topo {
+
+using bf16 = __nv_bfloat16;
 
 struct Ctx {
     cudaStream_t s;
@@ -50,6 +53,8 @@ struct VBuf {             // V-cycle work vectors of one level in one precision
 
 struct Level {
     Geom g;
+    bf16* ha = nullptr;       // BF16 V-cycle iterates (TOPO_MIXED_BF16, levels < L-1)
+    bf16* hb = nullptr;
     OpLaunch op32, op64;      // operator launch geometry per precision
     double scale = 1.0;       // 2^l
     double* rho = nullptr;    // homogenized density
@@ -74,6 +79,7 @@ struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
 
 struct Scalars {              // device-resident CG scalars
     double rz, rz_new, pq, rr, alpha, beta, ff, aux;
+    double rz_old;            // z.r of the previous iteration (flexible beta)
 };
 
 }  // namespace topo
@@ -116,7 +122,7 @@ struct topo_grid {
     double* partials = nullptr;     // reduction partials
     topo::Scalars* sc = nullptr;    // device scalars
     double* host_sc = nullptr;      // pinned host mirror
-    bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false;
+    bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false, bf16_ready = false;
     long long launches = 0;
     topo_solve_stats stats{};
     std::string err;
@@ -138,6 +144,13 @@ OpLaunch op_launch64(const Geom& g);
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
             const T* u, const T* f, T* out, T omega, double* dot_partials);
+// V-cycle operators with BF16 iterates and FP32 arithmetic: u BF16, f FP32,
+// output BF16 (out_h) or FP32 (out_f).  Instantiated: JACOBI0 -> BF16,
+// JACOBI -> BF16, JACOBI -> FP32 (with or without dot), RESID -> FP32;
+// returns -1 for any other combination, else as stencil().
+int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
+                 const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
+                 double* dot_partials);
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
                      double* A, int npad);
 // low = true: FP32 modal contraction of FP64-relative displacements (mixed modes)
@@ -151,6 +164,10 @@ void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const
 template <typename T>
 void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc,
                  const T* ec, T* uf);
+// uf (BF16) += P~ ec with FP32 arithmetic; ec FP32 (coarsest solve) or BF16
+template <typename TE>
+void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const TE* ec,
+                      bf16* uf);
 // coarse = scale * mean of the 8 children (densities: scale 1; moduli: scale 2)
 void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale);
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0,
@@ -167,6 +184,10 @@ void reduce_to(const Ctx& c, const double* partials, int n, double* dst);
 // CG scalar steps, all on device: alpha = rz/pq ; beta = rz_new/rz, rz = rz_new
 void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc);
 void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc);
+// flexible (Polak-Ribiere) beta for a preconditioner that varies between
+// applications: beta = z_new.(r_new - r_old) / z_old.r_old = -alpha z_new.q / rz_old,
+// from the partial sums of z_new.q; run after cg_beta
+void cg_beta_flexible(const Ctx& c, const double* partials_zq, int n, Scalars* sc);
 template <typename T>
 void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, const T* q, T* x, T* r,
                   double* partials);

@@ -9,6 +9,7 @@
 //     r = f - K x in FP64, solve K d ~= r in FP32, x += d, repeat.
 #include <chrono>
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "operator.cuh"
@@ -58,7 +59,7 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
         h->prof_kind.resize(h->prof_n + 1);
-        h->prof_kind[h->prof_n] = mode * 2 + (sizeof(T) == 4 ? 1 : 0);
+        h->prof_kind[h->prof_n] = mode * 4 + (sizeof(T) == 4 ? 1 : 0);
         ++h->prof_n;
     }
     return dot ? np : 0;
@@ -110,6 +111,100 @@ int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
 template int vcycle<double>(topo_grid*, int, const double*, double*, double*, double*);
 template int vcycle<float>(topo_grid*, int, const float*, float*, float*, double*);
 
+// operator launch with BF16 iterates; level-0 launches are recorded for
+// topo_profile_read (precision slot 2)
+static int op_apply_bf16(topo_grid* h, int mode, int l, const bf16* u, const float* f, bf16* out_h, float* out_f,
+                         double* dot) {
+    Level& lv = h->lev[l];
+    const bool rec = h->prof_on && l == 0 && h->prof_n < kProfMax;
+    if (rec) {
+        if ((int)h->prof_ev.size() < 2 * (h->prof_n + 1)) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            h->prof_ev.push_back(a);
+            h->prof_ev.push_back(b);
+        }
+        cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
+    }
+    const int np = stencil_bf16(h->ctx(), mode, lv.op32, *h->mk32, lv.E32, lv.mask, u, f, out_h, out_f,
+                                (float)h->prm.omega, dot);
+    if (rec) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
+        h->prof_kind.resize(h->prof_n + 1);
+        h->prof_kind[h->prof_n] = mode * 4 + 2;
+        ++h->prof_n;
+    }
+    return np;
+}
+
+// One level of the BF16 V-cycle (l < L-1).  The iterate lives in the level's
+// two BF16 buffers; the residual f - K u is formed in FP32 in v32.a and
+// restricted into the next level's FP32 right-hand side.  Returns the BF16
+// buffer holding the result, or, with out_f (level 0), writes the last
+// post-sweep to out_f in FP32 (and its dot f.out into *dot) and returns null.
+static bf16* vcycle_lp(topo_grid* h, int l, const float* f, float* out_f, double* dot, int* np) {
+    const Ctx c = h->ctx();
+    Level& lv = h->lev[l];
+    Level& lc = h->lev[l + 1];
+    const int pre = h->prm.pre, post = h->prm.post;
+    const long long n = 3 * lv.g.nn;
+    bf16* cur = lv.ha;
+    bf16* oth = lv.hb;
+    float* res = lv.v32.a;
+    if (pre > 0) {
+        op_apply_bf16(h, ST_JACOBI0, l, nullptr, f, cur, nullptr, nullptr);
+        for (int s = 1; s < pre; ++s) {
+            op_apply_bf16(h, ST_JACOBI, l, cur, f, oth, nullptr, nullptr);
+            bf16* t = cur; cur = oth; oth = t;
+        }
+        op_apply_bf16(h, ST_RESID, l, cur, f, nullptr, res, nullptr);
+    } else {
+        cudaMemsetAsync(cur, 0, sizeof(bf16) * n, h->stream);
+        cudaMemcpyAsync(res, f, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    restrict_residual<float>(c, lv.g, lv.mask, lc.mask, res, lc.v32.f);
+    if (l + 1 == h->L - 1) {
+        coarse_apply<float>(c, h->cs.n, h->cs.npad, h->cs.W32, h->cs.WT32, lc.v32.f, h->cs.y32, lc.v32.a);
+        prolong_add_bf16<float>(c, lv.g, lv.mask, lc.mask, lc.v32.a, cur);
+    } else {
+        int npc = 0;
+        const bf16* e = vcycle_lp(h, l + 1, lc.v32.f, nullptr, nullptr, &npc);
+        prolong_add_bf16<bf16>(c, lv.g, lv.mask, lc.mask, e, cur);
+    }
+    *np = 0;
+    for (int s = 0; s < post; ++s) {
+        if (out_f && s == post - 1) {
+            *np = op_apply_bf16(h, ST_JACOBI, l, cur, f, nullptr, out_f, dot);
+            return nullptr;
+        }
+        op_apply_bf16(h, ST_JACOBI, l, cur, f, oth, nullptr, nullptr);
+        bf16* t = cur; cur = oth; oth = t;
+    }
+    if (out_f) {   // no post-smoothing: widen the iterate
+        convert<bf16, float>(c, n, cur, out_f);
+        if (dot) {
+            dot_partials<float, float>(c, n, f, out_f, dot);
+            *np = kRedBlocks;
+        }
+        return nullptr;
+    }
+    return cur;
+}
+
+int vcycle_bf16(topo_grid* h, int l, const float* f, float* out, double* dot) {
+    const Ctx c = h->ctx();
+    Level& lv = h->lev[l];
+    if (l == h->L - 1) {   // single level: the direct solve
+        coarse_apply<float>(c, h->cs.n, h->cs.npad, h->cs.W32, h->cs.WT32, f, h->cs.y32, out);
+        if (dot) dot_partials<float, float>(c, 3 * lv.g.nn, f, out, dot);
+        return dot ? kRedBlocks : 0;
+    }
+    int np = 0;
+    vcycle_lp(h, l, f, out, dot, &np);
+    return dot ? np : 0;
+}
+
 // copies the scalars to the pinned mirror and waits for them
 static void fetch_scalars(topo_grid* h) {
     cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
@@ -133,7 +228,18 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
         return 0;
     }
     cudaMemsetAsync(&h->sc->aux, 0, sizeof(double), h->stream);
-    int np = vcycle<T>(h, 0, r, z, vb.a, h->partials);
+    // preconditioner: V-cycle in T, or with BF16 iterates (FP32 solves of
+    // TOPO_MIXED_BF16 handles)
+    auto precond = [&]() -> int {
+        if constexpr (std::is_same<T, float>::value) {
+            if (h->prm.precision == TOPO_MIXED_BF16)
+                return vcycle_bf16(h, 0, reinterpret_cast<const float*>(r), reinterpret_cast<float*>(z),
+                                   h->partials);
+        }
+        return vcycle<T>(h, 0, r, z, vb.a, h->partials);
+    };
+    const bool flexible = std::is_same<T, float>::value && h->prm.precision == TOPO_MIXED_BF16;
+    int np = precond();
     cg_beta(c, h->partials, np, h->sc);   // sets rz (beta unused on the first step)
     cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
     int it = 0;
@@ -150,8 +256,12 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
             break;
         }
         if (rr <= target_rr) break;
-        np = vcycle<T>(h, 0, r, z, vb.a, h->partials);
+        np = precond();
         cg_beta(c, h->partials, np, h->sc);
+        if (flexible) {   // BF16 rounding makes M^-1 vary slightly between applications
+            dot_partials<T, T>(c, n, z, q, h->partials);
+            cg_beta_flexible(c, h->partials, kRedBlocks, h->sc);
+        }
         cg_update_p<T>(c, n, h->sc, z, p);
     }
     if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;

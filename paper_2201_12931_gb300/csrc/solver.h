@@ -8,6 +8,11 @@ template <typename T>
 int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot);
 template <typename T>
 int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot);
+// V-cycle with BF16 iterates on levels 0 .. L-2 (FP32 arithmetic, FP32
+// right-hand sides and residuals, FP32 coarsest solve); the level-0 result
+// is written in FP32 to out.  f and out are level-0 FP32 vectors distinct
+// from the level's v32.a (used for the residual).
+int vcycle_bf16(topo_grid* h, int l, const float* f, float* out, double* dot);
 int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres);
 int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres);
 }  // namespace topo

@@ -50,6 +50,14 @@ __device__ __forceinline__ void ld3(const double* p, double* v) {
     v[1] = a.y;
     v[2] = p[2];
 }
+// vector element loads / stores with widening from and rounding to the
+// storage type (BF16 iterates of the V-cycle; arithmetic stays in T)
+__device__ __forceinline__ float ldv(const float* p) { return *p; }
+__device__ __forceinline__ double ldv(const double* p) { return *p; }
+__device__ __forceinline__ float ldv(const bf16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void stv(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stv(double* p, double v) { *p = v; }
+__device__ __forceinline__ void stv(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
@@ -57,10 +65,11 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // The per-plane body is a generic lambda called with a compile-time buffer
 // parity B = P & 1, so that double buffers and the two-plane register history
 // are addressed statically (no register moves, no dynamic indexing).
-template <typename T, int MODE, bool DOT>
+// T: arithmetic, f, E; TU: storage of u; TO: storage of the output.
+template <typename T, typename TU, typename TO, int MODE, bool DOT>
 __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
-    k_op(const ModalK<T> mk, const T* __restrict__ E, const uint8_t* __restrict__ mask, const T* __restrict__ u,
-         const T* __restrict__ f, T* __restrict__ out, const int nx, const int ny, const int nz, const int cz,
+    k_op(const ModalK<T> mk, const T* __restrict__ E, const uint8_t* __restrict__ mask, const TU* __restrict__ u,
+         const T* __restrict__ f, TO* __restrict__ out, const int nx, const int ny, const int nz, const int cz,
          const T omega, double* __restrict__ partials) {
     constexpr int TX = kOpTX, TY = op_ty<T>();
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
@@ -127,20 +136,20 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
         if (NEEDU || NEEDF) {
             const bool ok = pin && node_ok;
             sm[S] = ok ? mask[pb + own_xy] : 0u;
-            const T* ub = u + 3 * pb + own3;
+            const TU* ub = u + 3 * pb + own3;
             const T* fb_ = f + 3 * pb + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (NEEDU) su[S][c] = ok ? ub[c] : T(0);
+                if (NEEDU) su[S][c] = ok ? (T)ldv(ub + c) : T(0);
                 if (NEEDF) sf[S][c] = ok ? fb_[c] : T(0);
             }
         }
         if (NEEDU) {
             const bool okh = pin && halo_ok;
             shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
-            const T* hb = u + 3 * pb + halo3;
+            const TU* hb = u + 3 * pb + halo3;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? hb[c] : T(0);
+            for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
         }
         sE[S] = (col_ok && P >= 1 && P <= nz) ? E[(long long)(P - 1) * nx * ny + col_xy] : T(0);
     };
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 const T* e = Eb + ty * TX + tx;
                 rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
-            T* o = out + 3 * ((long long)Q * nplane) + own3;
+            TO* o = out + 3 * ((long long)Q * nplane) + own3;
             const unsigned m2 = sm[SO];
             T d32 = T(0);
 #pragma unroll
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                     r = omega * fo * (fixed ? T(1) : rD);
                     if (DOT) d32 += fo * r;
                 }
-                o[c] = r;
+                stv(o + c, r);
             }
             if (DOT) dot += (double)d32;
         }
@@ -290,15 +299,16 @@ constexpr size_t op_smem_bytes() {
     return sizeof(T) * (2 * (TY + 1) * (kOpTX + 1) * 4 + 2 * 3 * TY * kOpTX * 4 + 2 * TY * kOpTX);
 }
 
-template <typename T, int MODE, bool DOT>
-void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const T* u,
-               const T* f, T* out, T omega, double* dot) {
+template <typename T, int MODE, bool DOT, typename TU = T, typename TO = T>
+void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const TU* u,
+               const T* f, TO* out, T omega, double* dot) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_op<T, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)op_smem_bytes<T>());
+        cudaFuncSetAttribute(k_op<T, TU, TO, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)op_smem_bytes<T>());
         attr = true;
     }
-    k_op<T, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, op_ty<T>()), op_smem_bytes<T>(), c.s>>>(
+    k_op<T, TU, TO, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, op_ty<T>()), op_smem_bytes<T>(), c.s>>>(
         mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot);
     TOPO_LAUNCH_CHECK(c);
 }
@@ -439,6 +449,24 @@ template int stencil<double>(const Ctx&, int, const OpLaunch&, const ModalK<doub
                              const double*, const double*, double*, double, double*);
 template int stencil<float>(const Ctx&, int, const OpLaunch&, const ModalK<float>&, const float*, const uint8_t*,
                             const float*, const float*, float*, float, double*);
+
+int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
+                 const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
+                 double* dot) {
+    if (mode == ST_JACOBI0 && out_h && !dot) {
+        launch_op<float, ST_JACOBI0, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr);
+    } else if (mode == ST_JACOBI && out_h && !dot) {
+        launch_op<float, ST_JACOBI, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr);
+    } else if (mode == ST_JACOBI && out_f) {
+        if (dot) launch_op<float, ST_JACOBI, true, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, dot);
+        else launch_op<float, ST_JACOBI, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
+    } else if (mode == ST_RESID && out_f && !dot) {
+        launch_op<float, ST_RESID, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
+    } else {
+        return -1;   // combination not instantiated
+    }
+    return dot ? L.gx * L.gy * L.gz : 0;
+}
 
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
                      double* A, int npad) {

@@ -59,9 +59,10 @@ __global__ void k_restrict(const uint8_t* __restrict__ maskf, const uint8_t* __r
     for (int c = 0; c < 3; ++c) rc[3 * N + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
 }
 
-template <typename T>
+// T: arithmetic; TE / TU: storage of the coarse correction and the fine iterate
+template <typename T, typename TE = T, typename TU = T>
 __global__ void k_prolong_add(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
-                              const T* __restrict__ ec, T* __restrict__ uf, int nxf, int nyf, int nzf) {
+                              const TE* __restrict__ ec, TU* __restrict__ uf, int nxf, int nyf, int nzf) {
     const int NXf = nxf + 1, NYf = nyf + 1, NZf = nzf + 1;
     const int NXc = nxf / 2 + 1, NYc = nyf / 2 + 1;
     const long long nnf = (long long)NXf * NYf * NZf;
@@ -83,12 +84,12 @@ __global__ void k_prolong_add(const uint8_t* __restrict__ maskf, const uint8_t* 
                 const T w = wi * wj * wk;
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    if (!((mc >> c) & 1u)) acc[c] += w * ec[3 * N + c];
+                    if (!((mc >> c) & 1u)) acc[c] += w * (T)ec[3 * N + c];
             }
     const unsigned mf = maskf[n];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        if (!((mf >> c) & 1u)) uf[3 * n + c] += acc[c];
+        if (!((mf >> c) & 1u)) uf[3 * n + c] = (TU)((T)uf[3 * n + c] + acc[c]);
 }
 
 __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__ rc, int nxf, int nyf,
@@ -178,6 +179,15 @@ void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8
 template void prolong_add<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
                                   double*);
 template void prolong_add<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, float*);
+
+template <typename TE>
+void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const TE* ec,
+                      bf16* uf) {
+    k_prolong_add<float, TE, bf16><<<grid_for(gf.nn, 256), 256, 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void prolong_add_bf16<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, bf16*);
+template void prolong_add_bf16<bf16>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const bf16*, bf16*);
 
 void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale) {
     const long long nec = (long long)(gf.nx / 2) * (gf.ny / 2) * (gf.nz / 2);

@@ -72,6 +72,26 @@ def test_vcycle(dims, levels, precision, tol):
     assert rel_max(z, ref) < tol, rel_max(z, ref)
 
 
+@pytest.mark.parametrize("dims,levels", [((8, 4, 4), 2), ((48, 24, 24), 3), ((32, 16, 16), 4), ((6, 4, 4), 1)])
+def test_vcycle_bf16_iterates(dims, levels):
+    """V-cycle with BF16 iterates (FP32 arithmetic) against the oracle's FP64
+    V-cycle.  Each stored iterate is rounded to 8 significant bits (relative
+    2^-9); along one V-cycle an entry passes through at most pre + post + 1
+    roundings per level, so the relative 2-norm error stays below ~20 * 2^-9
+    = 0.04.  With one level the V-cycle is the FP32 direct solve (1e-4)."""
+    g, pb, rho, H = make_case(dims, levels, seed=4)
+    r = synth.uniform_field((H[0].K.shape[0], 1, 1), 12, -1, 1)
+    r[pb.fixed.astype(bool)] = 0.0
+    z = n(g.vcycle(t(r), precision=2))
+    ref = multigrid.vcycle(H, r, g.params.omega, g.params.pre, g.params.post)
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err < (1e-4 if levels == 1 else 4e-2), err
+    if levels > 1:
+        z32 = n(g.vcycle(t(r), precision=1))
+        assert np.linalg.norm(z32 - ref) / np.linalg.norm(ref) < err   # the rounding is visible
+    assert float(z @ r) > 0.0                                           # still a descent direction
+
+
 @pytest.mark.parametrize("dims,levels", [((48, 24, 24), 3), ((40, 24, 16), 4)])
 def test_modulus_averaging_variant(dims, levels):
     """Coarse moduli = mean of the children's moduli (homogenize = 1): the

@@ -36,7 +36,7 @@ def _gpu_solve(dims, levels, problem, rho, precision, tol):
     ((32, 16, 16), 4, "mbb"),
     ((12, 4, 4), 1, "cantilever"),
 ])
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_matches_oracle(dims, levels, problem, precision):
     rho = synth.uniform_field(dims, 1, 1e-3, 1.0)
     rho = oflt.density_filter(rho, dims, 1.5)
