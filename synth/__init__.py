@@ -176,6 +176,17 @@ WORKLOADS = {
         dims=(256, 128, 128), problem="cantilever", levels=5, precision="mixed_bf16",
         density=dict(kind="const", value=0.12), rel_tol=1e-8,
         oc=dict(iters=50, rmin=2.5, move=0.2, volfrac=0.12)),
+    # the cantilever cases of the paper's timing table (Sec. 5, Example 1):
+    # grid and iteration count from the table; volume fraction, filter
+    # radius and move limit are not stated there (TOP3D125-style defaults)
+    "cantilever_64x32x32_oc64": dict(
+        dims=(64, 32, 32), problem="cantilever", levels=4, precision="mixed",
+        density=dict(kind="const", value=0.12), rel_tol=1e-8,
+        oc=dict(iters=64, rmin=1.5, move=0.2, volfrac=0.12)),
+    "cantilever_128x64x64_oc49": dict(
+        dims=(128, 64, 64), problem="cantilever", levels=5, precision="mixed",
+        density=dict(kind="const", value=0.12), rel_tol=1e-8,
+        oc=dict(iters=49, rmin=1.5, move=0.2, volfrac=0.12)),
     "cantilever_768x384x384_mixed": dict(
         dims=(768, 384, 384), problem="cantilever", levels=7, precision="mixed",
         density=dict(kind="uniform_filtered_clipped", seed=3, lo=0.0, hi=1.0,
