@@ -166,7 +166,7 @@ void free_all(topo_grid* h) {
     F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
     F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
     F(h->K0d); F(h->K0f);
-    F(h->dc_work); F(h->dv_work); F(h->xnew_work); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
+    F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
     F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
     if (h->host_sc) cudaFreeHost(h->host_sc);
     delete h->mk64;
@@ -398,6 +398,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     TRY(dalloc(h, &h->K0f, 576));
     TRY(dalloc(h, &h->dc_work, g0.ne));
     TRY(dalloc(h, &h->xnew_work, g0.ne));
+    TRY(dalloc(h, &h->oc_hi, g0.ne));
     TRY(dalloc(h, &h->S_cache, g0.ne));
     TRY(dalloc(h, &h->dv_cache, g0.ne));
     TRY(dalloc(h, &h->lam, 8));
@@ -588,7 +589,8 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
     const Geom& g = h->lev[0].g;
     divide(c, g.ne, dc_dev, h->S_cache, h->xnew_work);
     filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dc_work, 1, nullptr);
-    oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, h->dc_work);
+    // q over dc_work, lower bounds in xnew_work, upper bounds in oc_hi
+    oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->xnew_work, h->oc_hi);
     const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
     const double init[8] = {l1, l2, 0.5 * (l1 + l2), (l2 - l1) / (l1 + l2) > tol ? 0.0 : 1.0, 0.0, 0.5 * (l1 + l2),
                             0.0, 0.0};
@@ -596,7 +598,7 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
     double state[8];
     for (int batch = 0; batch < 25; ++batch) {
         for (int k = 0; k < 16; ++k) {
-            oc_bisect_step(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->partials, h->lam);
+            oc_bisect_step(c, g.ne, h->xnew_work, h->oc_hi, h->dc_work, h->dv_cache, h->partials, h->lam);
             oc_bisect_finalize(c, h->partials, h->lam, volfrac * (double)g.ne, tol);
         }
         CK(h, cudaMemcpyAsync(state, h->lam, sizeof(state), cudaMemcpyDeviceToHost, h->stream));
@@ -604,7 +606,7 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
         if (state[3] != 0.0) break;
     }
     if (state[3] == 0.0) return fail(h, TOPO_MAXITER, "bisection did not converge");
-    oc_write(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->lam, h->partials, h->dtmp);
+    oc_write(c, g.ne, rho_dev_inout, h->xnew_work, h->oc_hi, h->dc_work, h->lam, h->partials, h->dtmp);
     if (change_out) {
         CK(h, cudaMemcpyAsync(change_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));

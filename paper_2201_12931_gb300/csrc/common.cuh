@@ -101,8 +101,8 @@ struct topo_grid {
     topo::ModalK<float>* mk32 = nullptr;
     long long npartials = 0;                // size of the partials buffer
     double* dc_work = nullptr;      // element work arrays (filter / OC)
-    double* dv_work = nullptr;
     double* xnew_work = nullptr;
+    double* oc_hi = nullptr;        // OC upper move-limit bounds
     double* S_cache = nullptr;      // filter weight sums S_e for S_radius
     double* dv_cache = nullptr;     // H^T 1 for S_radius
     int4* offs = nullptr;           // filter offsets for S_radius
@@ -214,12 +214,14 @@ void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* 
                    double* out, int mode, const double* S);
 void divide(const Ctx& c, long long n, const double* a, const double* b, double* out);
 // q = x sqrt(max(-dc~, 1e-30) / dv~)
-void oc_prepare(const Ctx& c, long long ne, const double* x, const double* dct, const double* dv, double* q);
-void oc_bisect_step(const Ctx& c, long long ne, const double* x, const double* num, const double* dv,
-                    double move, double* partials, double* lam_state);
+// q = x sqrt(max(-dc~,1e-30)/dv~) in place over dc~; lo / hi: move-limit bounds
+void oc_prepare(const Ctx& c, long long ne, const double* x, double* dct_q, const double* dv, double move, double* lo,
+                double* hi);
+void oc_bisect_step(const Ctx& c, long long ne, const double* lo, const double* hi, const double* num,
+                    const double* dv, double* partials, double* lam_state);
 void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state, double volfrac_ne,
                         double tol);
-void oc_write(const Ctx& c, long long ne, double* x, const double* num, const double* dv, double move,
+void oc_write(const Ctx& c, long long ne, double* x, const double* lo, const double* hi, const double* num,
               const double* lam_state, double* partials, double* change_dst);
 
 }  // namespace topo

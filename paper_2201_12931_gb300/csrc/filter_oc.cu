@@ -93,22 +93,32 @@ __global__ void k_divide(long long n, const double* __restrict__ a, const double
 
 // q_e = x_e sqrt(max(-dc~_e, 1e-30) / dv~_e): the part of the OC candidate
 // x (B)^(1/2), B = -dc~ / (lambda dv~), that does not depend on lambda
-__global__ void k_oc_prepare(long long ne, const double* __restrict__ x, const double* __restrict__ dct,
-                             const double* __restrict__ dv, double* __restrict__ q) {
+// q = x sqrt(max(-dc~, 1e-30) / dv~) (in place over dc~) and the move-limit
+// bounds lo = max(0, x - move), hi = min(1, x + move) of Eq. OC
+__global__ void k_oc_prepare(long long ne, const double* __restrict__ x, double* dct_q, const double* __restrict__ dv,
+                             double move, double* __restrict__ lo, double* __restrict__ hi) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= ne) return;
-    q[e] = x[e] * sqrt(fmax(-dct[e], 1e-30) / dv[e]);
+    const double xe = x[e];
+    dct_q[e] = xe * sqrt(fmax(-dct_q[e], 1e-30) / dv[e]);
+    lo[e] = fmax(0.0, xe - move);
+    hi[e] = fmin(1.0, xe + move);
 }
 
 // lam state: [0] l1, [1] l2, [2] lmid (next to evaluate), [3] done, [4] steps, [5] last lmid
-// candidate clamped to the move limits and [0, 1]; s = lambda^(-1/2)
-__device__ __forceinline__ double oc_candidate(double x, double q, double s, double move) {
-    return fmax(0.0, fmax(x - move, fmin(1.0, fmin(x + move, q * s))));
+// candidate min(hi, max(lo, q s)) with s = lambda^(-1/2); the three values are
+// non-negative, so the clamps compare their IEEE bit patterns as integers
+// (same order, exact, and off the FP64 pipe)
+__device__ __forceinline__ double oc_candidate(double q, double s, double lo, double hi) {
+    long long b = __double_as_longlong(q * s);
+    b = max(b, __double_as_longlong(lo));
+    b = min(b, __double_as_longlong(hi));
+    return __longlong_as_double(b);
 }
 
-__global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __restrict__ x, const double* __restrict__ num,
-                                                 const double* __restrict__ dv, double move, double* __restrict__ partials,
-                                                 const double* __restrict__ lam) {
+__global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __restrict__ lo, const double* __restrict__ hi,
+                                                 const double* __restrict__ num, const double* __restrict__ dv,
+                                                 double* __restrict__ partials, const double* __restrict__ lam) {
     __shared__ double sh[32];
     if (lam[3] != 0.0) {
         if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
@@ -117,7 +127,7 @@ __global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __r
     const double sl = rsqrt(lam[2]);
     double s = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
-        s += dv[e] * oc_candidate(x[e], num[e], sl, move);
+        s += dv[e] * oc_candidate(num[e], sl, lo[e], hi[e]);
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -141,15 +151,15 @@ __global__ void __launch_bounds__(1024) k_oc_finalize(const double* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) k_oc_write(long long ne, double* __restrict__ x, const double* __restrict__ num,
-                                                  const double* __restrict__ dv, double move, const double* __restrict__ lam,
-                                                  double* __restrict__ partials) {
+__global__ void __launch_bounds__(256) k_oc_write(long long ne, double* __restrict__ x, const double* __restrict__ lo,
+                                                  const double* __restrict__ hi, const double* __restrict__ num,
+                                                  const double* __restrict__ lam, double* __restrict__ partials) {
     __shared__ double sh[32];
     const double sl = rsqrt(lam[5]);
     double m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
         const double xo = x[e];
-        const double xn = oc_candidate(xo, num[e], sl, move);
+        const double xn = oc_candidate(num[e], sl, lo[e], hi[e]);
         m = fmax(m, fabs(xn - xo));
         x[e] = xn;
     }
@@ -183,14 +193,15 @@ void divide(const Ctx& c, long long n, const double* a, const double* b, double*
     TOPO_LAUNCH_CHECK(c);
 }
 
-void oc_prepare(const Ctx& c, long long ne, const double* x, const double* dct, const double* dv, double* q) {
-    k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, x, dct, dv, q);
+void oc_prepare(const Ctx& c, long long ne, const double* x, double* dct_q, const double* dv, double move, double* lo,
+                double* hi) {
+    k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, x, dct_q, dv, move, lo, hi);
     TOPO_LAUNCH_CHECK(c);
 }
 
-void oc_bisect_step(const Ctx& c, long long ne, const double* x, const double* num, const double* dv, double move,
-                    double* partials, double* lam_state) {
-    k_oc_step<<<kRedBlocks, 256, 0, c.s>>>(ne, x, num, dv, move, partials, lam_state);
+void oc_bisect_step(const Ctx& c, long long ne, const double* lo, const double* hi, const double* num,
+                    const double* dv, double* partials, double* lam_state) {
+    k_oc_step<<<kRedBlocks, 256, 0, c.s>>>(ne, lo, hi, num, dv, partials, lam_state);
     TOPO_LAUNCH_CHECK(c);
 }
 
@@ -199,9 +210,9 @@ void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state,
     TOPO_LAUNCH_CHECK(c);
 }
 
-void oc_write(const Ctx& c, long long ne, double* x, const double* num, const double* dv, double move,
+void oc_write(const Ctx& c, long long ne, double* x, const double* lo, const double* hi, const double* num,
               const double* lam_state, double* partials, double* change_dst) {
-    k_oc_write<<<kRedBlocks, 256, 0, c.s>>>(ne, x, num, dv, move, lam_state, partials);
+    k_oc_write<<<kRedBlocks, 256, 0, c.s>>>(ne, x, lo, hi, num, lam_state, partials);
     TOPO_LAUNCH_CHECK(c);
     k_max_to<<<1, 1024, 0, c.s>>>(partials, change_dst);
     TOPO_LAUNCH_CHECK(c);

@@ -21,6 +21,8 @@
 // also emit per-CTA FP64 partial sums of a dot product.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace topo {
@@ -41,30 +43,80 @@ constexpr int kOpTX = 32;
 template <typename T>
 __host__ __device__ constexpr int op_ty() { return 8; }
 
+// FP32 helpers: components x and y of a node travel as one float2 and are
+// combined with the paired FP32 instructions of sm_100+ (z stays scalar)
+__device__ __forceinline__ float2 ld2(const float* p) { return make_float2(p[0], p[1]); }
+__device__ __forceinline__ void st2(float* p, float2 v) {
+    p[0] = v.x;
+    p[1] = v.y;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ void face_forward(const T* c00, const T* c10, const T* c01, const T* c11, T* F) {
     // F[3*g + c], g = bx + 2 by
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 s0 = add2(ld2(c10), ld2(c00)), d0 = sub2(ld2(c10), ld2(c00));
+        const float2 s1 = add2(ld2(c11), ld2(c01)), d1 = sub2(ld2(c11), ld2(c01));
+        st2(F + 0, add2(s1, s0));
+        st2(F + 3, add2(d1, d0));
+        st2(F + 6, sub2(s1, s0));
+        st2(F + 9, sub2(d1, d0));
+        const float z0 = c10[2] + c00[2], e0 = c10[2] - c00[2];
+        const float z1 = c11[2] + c01[2], e1 = c11[2] - c01[2];
+        F[2] = z1 + z0;
+        F[5] = e1 + e0;
+        F[8] = z1 - z0;
+        F[11] = e1 - e0;
+    } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const T s0 = c10[c] + c00[c], d0 = c10[c] - c00[c];
-        const T s1 = c11[c] + c01[c], d1 = c11[c] - c01[c];
-        F[0 + c] = s1 + s0;
-        F[3 + c] = d1 + d0;
-        F[6 + c] = s1 - s0;
-        F[9 + c] = d1 - d0;
+        for (int c = 0; c < 3; ++c) {
+            const T s0 = c10[c] + c00[c], d0 = c10[c] - c00[c];
+            const T s1 = c11[c] + c01[c], d1 = c11[c] - c01[c];
+            F[0 + c] = s1 + s0;
+            F[3 + c] = d1 + d0;
+            F[6 + c] = s1 - s0;
+            F[9 + c] = d1 - d0;
+        }
     }
 }
 
 template <typename T>
 __device__ __forceinline__ void face_inverse(const T* A, T* c00, T* c10, T* c01, T* c11) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 lo0 = sub2(ld2(A + 0), ld2(A + 6)), hi0 = add2(ld2(A + 0), ld2(A + 6));
+        const float2 lo1 = sub2(ld2(A + 3), ld2(A + 9)), hi1 = add2(ld2(A + 3), ld2(A + 9));
+        st2(c00, sub2(lo0, lo1));
+        st2(c10, add2(lo0, lo1));
+        st2(c01, sub2(hi0, hi1));
+        st2(c11, add2(hi0, hi1));
+        const float l0 = A[2] - A[8], h0 = A[2] + A[8];
+        const float l1 = A[5] - A[11], h1 = A[5] + A[11];
+        c00[2] = l0 - l1;
+        c10[2] = l0 + l1;
+        c01[2] = h0 - h1;
+        c11[2] = h0 + h1;
+    } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const T lo0 = A[0 + c] - A[6 + c], hi0 = A[0 + c] + A[6 + c];   // bx = 0 : ay = 0 / 1
-        const T lo1 = A[3 + c] - A[9 + c], hi1 = A[3 + c] + A[9 + c];   // bx = 1
-        c00[c] = lo0 - lo1;
-        c10[c] = lo0 + lo1;
-        c01[c] = hi0 - hi1;
-        c11[c] = hi0 + hi1;
+        for (int c = 0; c < 3; ++c) {
+            const T lo0 = A[0 + c] - A[6 + c], hi0 = A[0 + c] + A[6 + c];   // bx = 0 : ay = 0 / 1
+            const T lo1 = A[3 + c] - A[9 + c], hi1 = A[3 + c] + A[9 + c];   // bx = 1
+            c00[c] = lo0 - lo1;
+            c10[c] = lo0 + lo1;
+            c01[c] = hi0 - hi1;
+            c11[c] = hi0 + hi1;
+        }
     }
 }
 
@@ -73,13 +125,23 @@ __device__ __forceinline__ void face_inverse(const T* A, T* c00, T* c10, T* c01,
 template <typename T>
 __device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* FB, const T* FT, T* Bo, T* To) {
     T m[24];
+    if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-    for (int g = 0; g < 4; ++g)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            m[3 * g + c] = FT[3 * g + c] + FB[3 * g + c];
-            m[3 * (g + 4) + c] = FT[3 * g + c] - FB[3 * g + c];
+        for (int g = 0; g < 4; ++g) {
+            st2(m + 3 * g, add2(ld2(FT + 3 * g), ld2(FB + 3 * g)));
+            st2(m + 3 * (g + 4), sub2(ld2(FT + 3 * g), ld2(FB + 3 * g)));
+            m[3 * g + 2] = FT[3 * g + 2] + FB[3 * g + 2];
+            m[3 * (g + 4) + 2] = FT[3 * g + 2] - FB[3 * g + 2];
         }
+    } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                m[3 * g + c] = FT[3 * g + c] + FB[3 * g + c];
+                m[3 * (g + 4) + c] = FT[3 * g + c] - FB[3 * g + c];
+            }
+    }
     const T nd = E * k.nd, no = E * k.no, sc = E * k.sc, bp = E * k.bp, bq = E * k.bq;
     const T td = E * k.td, to = E * k.to, cg = E * k.cg;
     T w[24];
@@ -117,13 +179,23 @@ __device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* 
         Bo[c] = -w[12 + c];
         To[c] = w[12 + c];
     }
+    if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-    for (int g = 1; g < 4; ++g)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Bo[3 * g + c] = w[3 * g + c] - w[3 * (g + 4) + c];
-            To[3 * g + c] = w[3 * g + c] + w[3 * (g + 4) + c];
+        for (int g = 1; g < 4; ++g) {
+            st2(Bo + 3 * g, sub2(ld2(w + 3 * g), ld2(w + 3 * (g + 4))));
+            st2(To + 3 * g, add2(ld2(w + 3 * g), ld2(w + 3 * (g + 4))));
+            Bo[3 * g + 2] = w[3 * g + 2] - w[3 * (g + 4) + 2];
+            To[3 * g + 2] = w[3 * g + 2] + w[3 * (g + 4) + 2];
         }
+    } else {
+#pragma unroll
+        for (int g = 1; g < 4; ++g)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Bo[3 * g + c] = w[3 * g + c] - w[3 * (g + 4) + c];
+                To[3 * g + c] = w[3 * g + c] + w[3 * (g + 4) + c];
+            }
+    }
 }
 
 }  // namespace topo
