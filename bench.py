@@ -48,8 +48,9 @@ def parse_args(argv=None):
                     help="relative residual of the timed all-FP64 comparison solve")
     ap.add_argument("--fp64-ref", choices=["full", "skip"], default="full")
     ap.add_argument("--cpu-baseline", choices=["on", "off"], default="on")
-    ap.add_argument("--coarsening", choices=["density", "modulus"], default="density",
-                    help="coarse moduli from the mean child density (Sec. 4.2.2) or the mean child modulus")
+    ap.add_argument("--coarsening", choices=["density", "modulus", "galerkin"], default="density",
+                    help="coarse operators: SIMP of the mean child density (Sec. 4.2.2), mean child modulus, "
+                         "or stored Galerkin element matrices")
     ap.add_argument("--oc-loop", action="store_true",
                     help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
@@ -314,6 +315,9 @@ def ku_roofline(rows, peak, src, ne):
     return roofline_entry(r[0], peak, src, ne) if r else None
 
 
+COARSENING = {"density": 0, "modulus": 1, "galerkin": 2}
+
+
 def max_over_ranks(vals, dev=None):
     """Element-wise maximum of a list of floats over all ranks of the default
     process group (the replicas' times); the list itself without a group."""
@@ -352,7 +356,7 @@ def run_ours(args):
     rmin = w.get("oc", {}).get("rmin", w["density"].get("rmin", 1.5))
     move = w.get("oc", {}).get("move", 0.2)
 
-    hom = 1 if args.coarsening == "modulus" else 0
+    hom = COARSENING[args.coarsening]
     g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom))
     rho0 = physical_density(g, args.workload, dims, dev)
     volfrac = w.get("oc", {}).get("volfrac", float(rho0.mean()))
@@ -510,7 +514,7 @@ def run_oc_loop(args):
            "volfrac": oc["volfrac"], "coarsening": args.coarsening}
     runs = {}
     for label, p in (("mixed", prec), ("fp64", TOPO_FP64)):
-        g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=1 if args.coarsening == "modulus" else 0))
+        g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=COARSENING[args.coarsening]))
         g.set_bc_loads(fixed_d, f_d)
         x = x0.clone()
         dc = torch.empty(ne, dtype=torch.float64, device=dev)

@@ -71,9 +71,12 @@ typedef struct {
                         /* the last one asks only for twice what is still missing */
     int inner_max_it;   /* iteration cap of each inner solve (500)                 */
     int max_refine;     /* cap on outer refinement steps (12)                      */
-    int homogenize;     /* coarse modulus rule (Sec. 4.2.2): 0 = SIMP of the mean   */
-                        /* of the 8 children's densities (the paper's rule,       */
-                        /* default); 1 = mean of the children's moduli            */
+    int homogenize;     /* coarse operators (Sec. 4.2.2): 0 = SIMP of the mean of  */
+                        /* the 8 children's densities (the paper's homogenization, */
+                        /* default); 1 = mean of the children's moduli; 2 =       */
+                        /* Galerkin P^T K P, stored as coarse element matrices    */
+                        /* (576 FP64 + 576 FP32 values per coarse element, levels */
+                        /* 1 .. L-1; not with TOPO_MIXED_BF16)                    */
 } topo_params;
 
 /* Fills *p with the defaults listed above.  TOPO_BADARG if p is NULL. */

@@ -159,7 +159,7 @@ void free_all(topo_grid* h) {
         F(l.rho); F(l.E64); F(l.E32); F(l.mask);
         F(l.v64.a); F(l.v64.b); F(l.v64.f);
         F(l.v32.a); F(l.v32.b); F(l.v32.f);
-        F(l.ha); F(l.hb);
+        F(l.ha); F(l.hb); F(l.Ke64); F(l.Ke32);
     }
     F(h->cs.A); F(h->cs.W64); F(h->cs.WT64); F(h->cs.W32); F(h->cs.WT32); F(h->cs.y64); F(h->cs.y32);
     F(h->cs.info);
@@ -199,7 +199,8 @@ topo_status ensure_coarse(topo_grid* h) {
         ALLOC(h, cs.y32, cs.npad);
         ALLOC(h, cs.info, 1);
     }
-    assemble_coarse(c, lc.g, h->K0d, lc.E64, lc.mask, cs.A, cs.npad);
+    assemble_coarse(c, lc.g, h->K0d, lc.E64, h->prm.homogenize == 2 && h->L > 1 ? lc.Ke64 : nullptr, lc.mask, cs.A,
+                    cs.npad);
     chol_factor(c, cs.A, cs.npad, cs.info);
     int info = 0;
     CK(h, cudaMemcpyAsync(&info, cs.info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -336,7 +337,9 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     if (p.precision < TOPO_FP64 || p.precision > TOPO_MIXED_BF16) return fail(nullptr, TOPO_BADARG, "bad precision");
     if (!(p.inner_tol > 0.0 && p.inner_tol < 1.0) || p.inner_max_it < 1 || p.max_refine < 1)
         return fail(nullptr, TOPO_BADARG, "bad inner solver parameters");
-    if (p.homogenize != 0 && p.homogenize != 1) return fail(nullptr, TOPO_BADARG, "homogenize must be 0 or 1");
+    if (p.homogenize < 0 || p.homogenize > 2) return fail(nullptr, TOPO_BADARG, "homogenize must be 0, 1 or 2");
+    if (p.homogenize == 2 && p.precision == TOPO_MIXED_BF16)
+        return fail(nullptr, TOPO_BADARG, "homogenize = 2 (stored Galerkin operators) is not combined with BF16 iterates");
     if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))
         return fail(nullptr, TOPO_BADARG, "grid too large");
 
@@ -453,9 +456,18 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
     const Ctx c = h->ctx();
     CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
     CK(h, cudaMemcpyAsync(h->lev[0].rho, rho_dev, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->prm.homogenize == 2 && h->L > 1) {   // stored Galerkin element matrices of levels 1 .. L-1
+        galerkin_init_constants();
+        for (int l = 1; l < h->L; ++l) {
+            Level& lv = h->lev[l];
+            // both copies: FP32 level operators can be requested on any handle
+            if (!lv.Ke64) ALLOC(h, lv.Ke64, 576 * lv.g.ne);
+            if (!lv.Ke32) ALLOC(h, lv.Ke32, 576 * lv.g.ne);
+        }
+    }
     for (int l = 0; l < h->L; ++l) {
         Level& lv = h->lev[l];
-        if (l == 0 || h->prm.homogenize == 0)
+        if (l == 0 || h->prm.homogenize != 1)
             simp_moduli(c, lv.g.ne, lv.rho, lv.scale, h->prm.E0, h->prm.Emin, h->prm.penal, lv.E64, lv.E32,
                         h->dflag);
         if (l + 1 < h->L) {
@@ -465,6 +477,14 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
                 homogenize(c, lv.g, lv.E64, lc.E64, 2.0);
                 convert<double, float>(c, lc.g.ne, lc.E64, lc.E32);
             }
+        }
+    }
+    if (h->prm.homogenize == 2) {
+        for (int l = 1; l < h->L; ++l) {
+            Level& lv = h->lev[l];
+            Level& lf = h->lev[l - 1];
+            galerkin_build(c, lf.g, h->K0d, lf.E64, l == 1 ? nullptr : lf.Ke64, lv.Ke64);
+            convert<double, float>(c, 576 * lv.g.ne, lv.Ke64, lv.Ke32);
         }
     }
     CK(h, cudaGetLastError());

@@ -55,6 +55,8 @@ struct Level {
     Geom g;
     bf16* ha = nullptr;       // BF16 V-cycle iterates (TOPO_MIXED_BF16, levels < L-1)
     bf16* hb = nullptr;
+    double* Ke64 = nullptr;   // stored Galerkin element matrices (homogenize = 2, levels >= 1)
+    float* Ke32 = nullptr;
     OpLaunch op32, op64;      // operator launch geometry per precision
     double scale = 1.0;       // 2^l
     double* rho = nullptr;    // homogenized density
@@ -151,8 +153,18 @@ int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, cons
 int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
                  const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
                  double* dot_partials);
-void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
-                     double* A, int npad);
+// dense coarsest operator from E_e K0, or from stored element matrices Ke (non-null)
+void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const double* Ke,
+                     const uint8_t* mask, double* A, int npad);
+// ---- galerkin.cu: stored Galerkin coarse element matrices ------------------
+void galerkin_init_constants();
+// Kc (coarse elements of the level below gf) = sum_o P_o^T Kchild P_o; the
+// children are Ef[e] K0 (Kf null) or Kf[e] (576 per element, element-major)
+void galerkin_build(const Ctx& c, const Geom& gf, const double* K0, const double* Ef, const double* Kf, double* Kc);
+// the operator modes of stencil() on a level given by element matrices (no dot)
+template <typename T>
+void elem_op(const Ctx& c, int mode, const Geom& g, const T* Ke, const uint8_t* mask, const T* u, const T* f, T* out,
+             T omega);
 // low = true: FP32 modal contraction of FP64-relative displacements (mixed modes)
 void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
                          double E0, double Emin, double penal, double* dc_out, double* partials, bool low);

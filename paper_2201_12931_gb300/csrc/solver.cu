@@ -28,6 +28,7 @@ struct P<double> {
     static const double* W(topo_grid* h) { return h->cs.W64; }
     static const double* WT(topo_grid* h) { return h->cs.WT64; }
     static double* y(topo_grid* h) { return h->cs.y64; }
+    static const double* Ke(Level& l) { return l.Ke64; }
 };
 template <>
 struct P<float> {
@@ -38,6 +39,7 @@ struct P<float> {
     static const float* W(topo_grid* h) { return h->cs.W32; }
     static const float* WT(topo_grid* h) { return h->cs.WT32; }
     static float* y(topo_grid* h) { return h->cs.y32; }
+    static const float* Ke(Level& l) { return l.Ke32; }
 };
 
 template <typename T>
@@ -54,8 +56,21 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
         }
         cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
     }
-    const int np = stencil<T>(h->ctx(), mode, P<T>::op(lv), P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
-                              (T)h->prm.omega, dot);
+    int np = 0;
+    if (h->prm.homogenize == 2 && l > 0) {   // stored Galerkin element matrices (no fused dot on coarse levels)
+        if (!P<T>::Ke(lv)) {   // not built: set_density forms them; never launch on a null matrix
+            set_global_error("Galerkin element matrices missing (set the density first)");
+            return 0;
+        }
+        elem_op<T>(h->ctx(), mode, lv.g, P<T>::Ke(lv), lv.mask, u, f, out, (T)h->prm.omega);
+        if (dot) {
+            dot_partials<T, T>(h->ctx(), 3 * lv.g.nn, mode == ST_APPLY ? u : (mode == ST_RESID ? out : f), out, dot);
+            np = kRedBlocks;
+        }
+    } else {
+        np = stencil<T>(h->ctx(), mode, P<T>::op(lv), P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
+                        (T)h->prm.omega, dot);
+    }
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
         h->prof_kind.resize(h->prof_n + 1);

@@ -321,20 +321,22 @@ void launch_mode(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* 
 }
 
 // Dense assembly of the coarsest operator with identity Dirichlet rows.
+// element matrices E_e K0, or the stored Ke[e] of a Galerkin level
 __global__ void k_assemble(const double* __restrict__ K0, const double* __restrict__ E,
-                           const uint8_t* __restrict__ mask, double* __restrict__ A, int nx, int ny, int nz,
-                           int npad) {
+                           const double* __restrict__ Ke, const uint8_t* __restrict__ mask, double* __restrict__ A,
+                           int nx, int ny, int nz, int npad) {
     const int e = blockIdx.x;
     const int i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
     const int NX = nx + 1, NY = ny + 1;
-    const double Ee = E[e];
+    const double Ee = Ke ? 0.0 : E[e];
     for (int t = threadIdx.x; t < 576; t += blockDim.x) {
         const int r = t / 24, s = t % 24;
         const int ar = r / 3, cr = r % 3, as = s / 3, cs = s % 3;
         const int nr = (i + (ar & 1)) + NX * ((j + ((ar >> 1) & 1)) + NY * (k + (ar >> 2)));
         const int ns = (i + (as & 1)) + NX * ((j + ((as >> 1) & 1)) + NY * (k + (as >> 2)));
         if (((mask[nr] >> cr) & 1u) || ((mask[ns] >> cs) & 1u)) continue;
-        atomicAdd(&A[(long long)(3 * nr + cr) * npad + (3 * ns + cs)], Ee * K0[r * 24 + s]);
+        atomicAdd(&A[(long long)(3 * nr + cr) * npad + (3 * ns + cs)],
+                  Ke ? Ke[(long long)e * 576 + t] : Ee * K0[r * 24 + s]);
     }
 }
 
@@ -468,10 +470,10 @@ int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>&
     return dot ? L.gx * L.gy * L.gz : 0;
 }
 
-void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const uint8_t* mask,
-                     double* A, int npad) {
+void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const double* Ke,
+                     const uint8_t* mask, double* A, int npad) {
     cudaMemsetAsync(A, 0, sizeof(double) * (size_t)npad * npad, c.s);
-    k_assemble<<<(unsigned)g.ne, 128, 0, c.s>>>(K0, E, mask, A, g.nx, g.ny, g.nz, npad);
+    k_assemble<<<(unsigned)g.ne, 128, 0, c.s>>>(K0, E, Ke, mask, A, g.nx, g.ny, g.nz, npad);
     TOPO_LAUNCH_CHECK(c);
     k_assemble_diag<<<(npad + 255) / 256, 256, 0, c.s>>>(mask, A, (int)(3 * g.nn), npad);
     TOPO_LAUNCH_CHECK(c);

@@ -25,6 +25,12 @@ def make_case(dims, levels, problem="cantilever", seed=3, lo=1e-3, hi=1.0, preci
     g.set_density(torch.tensor(rho, device=dev))
     g.set_bc_loads(torch.tensor(pb.fixed, device=dev), torch.tensor(pb.f, device=dev))
     K0 = element.element_stiffness(g.params.nu)
+    if g.params.homogenize == 2:
+        from oracle import assemble
+        E = assemble.simp_modulus(rho, g.params.E0, g.params.Emin, g.params.penal)
+        K = assemble.apply_dirichlet(assemble.assemble(dims, E, K0), pb.fixed)
+        H = multigrid.galerkin_hierarchy(dims, K, pb.fixed, levels)
+        return g, pb, rho, H
     rule = "modulus" if g.params.homogenize == 1 else "density"
     H = multigrid.homogenized_hierarchy(dims, rho, pb.fixed, K0, levels, g.params.E0, g.params.Emin,
                                         g.params.penal, rule=rule)

@@ -76,9 +76,14 @@ def test_create_grid_rejects_bad_omega_and_nu(lib):
     assert lib.topo_create_grid(2, 2, 2, C.byref(p), None, C.byref(h)) == 1
     lib.topo_default_params(C.byref(p))
     p.levels = 1
-    p.homogenize = 2
+    p.homogenize = 3
     assert lib.topo_create_grid(2, 2, 2, C.byref(p), None, C.byref(h)) == 1
     assert "homogenize" in lib.topo_last_error(None).decode()
+    lib.topo_default_params(C.byref(p))
+    p.levels = 1
+    p.homogenize = 2
+    p.precision = 2
+    assert lib.topo_create_grid(2, 2, 2, C.byref(p), None, C.byref(h)) == 1
 
 
 def test_null_handle_calls_are_rejected(lib):

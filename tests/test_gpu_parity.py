@@ -109,6 +109,32 @@ def test_modulus_averaging_variant(dims, levels):
     assert rel_max(n(g.vcycle(t(r), precision=0)), ref) < 1e-10
 
 
+@pytest.mark.parametrize("dims,levels,problem", [((8, 4, 4), 2, "cantilever"), ((48, 24, 24), 3, "cantilever"),
+                                                 ((40, 24, 16), 4, "cantilever"), ((32, 16, 16), 3, "mbb")])
+def test_galerkin_levels(dims, levels, problem):
+    """Stored Galerkin coarse element matrices (homogenize = 2): every
+    level's operator, Jacobi sweep and residual, and the V-cycle, against the
+    oracle's assembled Galerkin hierarchy P~^T K P~ (FP64 1e-12 / 1e-10,
+    FP32 1e-5 / 1e-4)."""
+    g, pb, rho, H = make_case(dims, levels, problem=problem, seed=6, lo=1e-3, hi=1.0, homogenize=2)
+    for l in range(levels):
+        nl = H[l].K.shape[0]
+        u = synth.uniform_field((nl, 1, 1), 300 + l, -1.0, 1.0)
+        f = synth.uniform_field((nl, 1, 1), 310 + l, -1.0, 1.0)
+        f[H[l].fixed.astype(bool)] = 0.0
+        ref = H[l].K @ u
+        assert rel_max(n(g.apply_operator(t(u), level=l, precision=0)), ref) < 1e-12, l
+        assert rel_max(n(g.apply_operator(t(u), level=l, precision=1)), ref) < 1e-5, l
+        assert rel_max(n(g.jacobi_sweep(t(u), t(f), level=l, precision=0)),
+                       multigrid.jacobi(H[l], u, f, g.params.omega)) < 1e-12, l
+        assert rel_max(n(g.residual(t(u), t(f), level=l, precision=0)), f - ref) < 1e-12, l
+    r = synth.uniform_field((H[0].K.shape[0], 1, 1), 14, -1, 1)
+    r[pb.fixed.astype(bool)] = 0.0
+    ref = multigrid.vcycle(H, r, g.params.omega, g.params.pre, g.params.post)
+    assert rel_max(n(g.vcycle(t(r), precision=0)), ref) < 1e-10
+    assert rel_max(n(g.vcycle(t(r), precision=1)), ref) < 1e-4
+
+
 @pytest.mark.parametrize("r", [1.5, 2.0, 2.5, 3.0])
 @pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 9)])
 def test_filter_and_transpose(r, dims):

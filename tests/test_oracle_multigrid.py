@@ -72,6 +72,20 @@ def test_galerkin_identity_uniform_density(problem):
     assert np.abs(Kg - H[1].K.toarray()).max() < 1e-12 * np.abs(Kg).max()
 
 
+@pytest.mark.parametrize("problem", ["cantilever", "mbb"])
+def test_galerkin_hierarchy_equals_rediscretisation_for_uniform_density(problem):
+    """Pins galerkin_hierarchy (assembled P~^T K P~) against the independent
+    rediscretisation with 2^l K0 on three levels: they coincide for uniform
+    stiffness."""
+    dims = (8, 8, 4) if problem == "cantilever" else (8, 4, 4)
+    pb = synth.cantilever(dims) if problem == "cantilever" else synth.mbb_half(dims)
+    rho = np.full(grid.n_elems(dims), 0.6)
+    Hh = multigrid.homogenized_hierarchy(dims, rho, pb.fixed, K0, levels=3)
+    Hg = multigrid.galerkin_hierarchy(dims, Hh[0].K, pb.fixed, levels=3)
+    for a, b in zip(Hg, Hh):
+        assert np.abs((a.K - b.K).toarray()).max() < 1e-12 * np.abs(b.K.toarray()).max()
+
+
 def test_homogenized_density_is_child_mean():
     dims = (4, 2, 2)
     rho = synth.uniform_field(dims, 11)
