@@ -508,6 +508,9 @@ def run_oc_loop(args):
     ne = dims[0] * dims[1] * dims[2]
     x0 = torch.tensor(synth.raw_density(name, dims), device=dev)
     prec = {"fp64": TOPO_FP64, "mixed": TOPO_MIXED, "mixed_bf16": TOPO_MIXED_BF16}[w["precision"]]
+    plabel = w["precision"]
+    if prec == TOPO_MIXED_BF16 and args.coarsening == "galerkin":   # stored Galerkin levels run FP32 iterates
+        prec, plabel = TOPO_MIXED, "mixed"
     tol = w.get("rel_tol", 1e-8)
     out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
            "iterations": oc["iters"], "rel_tol": tol, "rmin": oc["rmin"], "move": oc["move"],
@@ -535,7 +538,7 @@ def run_oc_loop(args):
         runs[label] = dict(C=Cs, iters=its, ms=ms)
         out[label] = {"ms_per_iteration": round(statistics.mean(ms), 3), "total_s": round(sum(ms) / 1e3, 3),
                       "pcg_iterations": its, "compliance_first": Cs[0], "compliance_last": Cs[-1],
-                      "precision": label if label == "fp64" else w["precision"]}
+                      "precision": label if label == "fp64" else plabel}
     drift = [abs(a - b) / abs(b) for a, b in zip(runs["mixed"]["C"], runs["fp64"]["C"])]
     out["compliance_drift_max"] = max(drift)
     out["compliance_drift_last"] = drift[-1]

@@ -166,7 +166,7 @@ void free_all(topo_grid* h) {
     F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
     F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
     F(h->K0d); F(h->K0f);
-    F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
+    F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->G64); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
     F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
     if (h->host_sc) cudaFreeHost(h->host_sc);
     delete h->mk64;
@@ -458,6 +458,15 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
     CK(h, cudaMemcpyAsync(h->lev[0].rho, rho_dev, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToDevice, h->stream));
     if (h->prm.homogenize == 2 && h->L > 1) {   // stored Galerkin element matrices of levels 1 .. L-1
         galerkin_init_constants();
+        if (!h->G64) {
+            double K0[576];
+            element_matrix(h->prm.nu, K0);
+            std::vector<double> G(8 * 576);
+            galerkin_child_matrices(K0, G.data());
+            ALLOC(h, h->G64, 8 * 576);
+            CK(h, cudaMemcpyAsync(h->G64, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));   // G goes out of scope
+        }
         for (int l = 1; l < h->L; ++l) {
             Level& lv = h->lev[l];
             // both copies: FP32 level operators can be requested on any handle
@@ -483,7 +492,7 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
         for (int l = 1; l < h->L; ++l) {
             Level& lv = h->lev[l];
             Level& lf = h->lev[l - 1];
-            galerkin_build(c, lf.g, h->K0d, lf.E64, l == 1 ? nullptr : lf.Ke64, lv.Ke64);
+            galerkin_build(c, lf.g, h->K0d, h->G64, lf.E64, l == 1 ? nullptr : lf.Ke64, lv.Ke64);
             convert<double, float>(c, 576 * lv.g.ne, lv.Ke64, lv.Ke32);
         }
     }

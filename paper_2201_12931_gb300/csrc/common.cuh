@@ -105,6 +105,7 @@ struct topo_grid {
     double* dc_work = nullptr;      // element work arrays (filter / OC)
     double* xnew_work = nullptr;
     double* oc_hi = nullptr;        // OC upper move-limit bounds
+    double* G64 = nullptr;          // Galerkin child matrices P_o^T K0 P_o (homogenize = 2)
     double* S_cache = nullptr;      // filter weight sums S_e for S_radius
     double* dv_cache = nullptr;     // H^T 1 for S_radius
     int4* offs = nullptr;           // filter offsets for S_radius
@@ -158,9 +159,13 @@ void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double
                      const uint8_t* mask, double* A, int npad);
 // ---- galerkin.cu: stored Galerkin coarse element matrices ------------------
 void galerkin_init_constants();
+// host: the 8 child matrices G_o = P_o^T K0 P_o (8 x 576, o-major)
+void galerkin_child_matrices(const double* K0, double* G);
 // Kc (coarse elements of the level below gf) = sum_o P_o^T Kchild P_o; the
-// children are Ef[e] K0 (Kf null) or Kf[e] (576 per element, element-major)
-void galerkin_build(const Ctx& c, const Geom& gf, const double* K0, const double* Ef, const double* Kf, double* Kc);
+// children are Ef[e] K0 (Kf null: scaled sum of G) or Kf[e] (576 per
+// element, element-major)
+void galerkin_build(const Ctx& c, const Geom& gf, const double* K0, const double* G, const double* Ef, const double* Kf,
+                    double* Kc);
 // the operator modes of stencil() on a level given by element matrices (no dot)
 template <typename T>
 void elem_op(const Ctx& c, int mode, const Geom& g, const T* Ke, const uint8_t* mask, const T* u, const T* f, T* out,

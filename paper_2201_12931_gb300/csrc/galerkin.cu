@@ -26,6 +26,25 @@ namespace topo {
 namespace {
 
 __constant__ double c_Q[8 * 64];   // Q_o[b][a], o-major
+// Level 1: Ke_1(E) = sum_o E_child(o) G_o with G_o = P_o^T K0 P_o (o-major,
+// 8 x 576), one thread per (coarse element, entry)
+__global__ void k_galerkin_build1(const double* __restrict__ G, const double* __restrict__ Ef, double* __restrict__ Kc,
+                                  int nxf, int nyf, int nzf) {
+    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
+    const long long total = (long long)nxc * nyc * nzc * 576;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const long long E = t / 576;
+    const int q = (int)(t % 576);
+    const int I = (int)(E % nxc), J = (int)((E / nxc) % nyc), K = (int)(E / ((long long)nxc * nyc));
+    double v = 0.0;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const long long ec = (2 * I + (o & 1)) + (long long)nxf * ((2 * J + ((o >> 1) & 1)) + (long long)nyf * (2 * K + (o >> 2)));
+        v += Ef[ec] * G[o * 576 + q];
+    }
+    Kc[t] = v;
+}
 
 // One CTA per coarse element E: Ke_{l+1}(E) = sum_o P_o^T Kc_o P_o by the
 // Kronecker form: T = Kc Q_o (per 3x3 component block), then Q_o^T T.
@@ -120,14 +139,7 @@ __global__ void __launch_bounds__(256) k_elem_op(const T* __restrict__ Ke, const
 
 }  // namespace
 
-// the interpolation blocks live in constant memory of each device (call
-// with the device current)
-void galerkin_init_constants() {
-    static bool done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && done[dev]) return;
-    double Q[8 * 64];
+static void interpolation_blocks(double* Q) {
     for (int o = 0; o < 8; ++o)
         for (int b = 0; b < 8; ++b)
             for (int a = 0; a < 8; ++a) {
@@ -140,13 +152,46 @@ void galerkin_init_constants() {
                 }
                 Q[o * 64 + b * 8 + a] = w;
             }
+}
+
+// Q_o in constant memory of each device (call with the device current)
+void galerkin_init_constants() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && done[dev]) return;
+    double Q[8 * 64];
+    interpolation_blocks(Q);
     cudaMemcpyToSymbol(c_Q, Q, sizeof(Q));
     if (dev < 64) done[dev] = true;
 }
 
-void galerkin_build(const Ctx& c, const Geom& gf, const double* K0, const double* Ef, const double* Kf, double* Kc) {
+// G_o = P_o^T K0 P_o on the host: G[o*576 + (3a + c)*24 + 3a' + d] =
+// sum_{b, b'} Q_o[b][a] K0[3b + c][3b' + d] Q_o[b'][a']
+void galerkin_child_matrices(const double* K0, double* G) {
+    double Q[8 * 64];
+    interpolation_blocks(Q);
+    for (int o = 0; o < 8; ++o)
+        for (int r = 0; r < 24; ++r)
+            for (int col = 0; col < 24; ++col) {
+                const int a = r / 3, c = r % 3, ap = col / 3, d = col % 3;
+                double v = 0.0;
+                for (int b = 0; b < 8; ++b)
+                    for (int bp = 0; bp < 8; ++bp)
+                        v += Q[o * 64 + b * 8 + a] * K0[(3 * b + c) * 24 + 3 * bp + d] * Q[o * 64 + bp * 8 + ap];
+                G[o * 576 + r * 24 + col] = v;
+            }
+}
+
+void galerkin_build(const Ctx& c, const Geom& gf, const double* K0, const double* G, const double* Ef, const double* Kf,
+                    double* Kc) {
     const long long nec = (long long)(gf.nx / 2) * (gf.ny / 2) * (gf.nz / 2);
-    k_galerkin_build<<<(unsigned)nec, 192, 0, c.s>>>(K0, Ef, Kf, Kc, gf.nx, gf.ny, gf.nz);
+    if (!Kf) {   // children on level 0: scaled sum of the constant G_o
+        const long long total = nec * 576;
+        k_galerkin_build1<<<(unsigned)((total + 255) / 256), 256, 0, c.s>>>(G, Ef, Kc, gf.nx, gf.ny, gf.nz);
+    } else {
+        k_galerkin_build<<<(unsigned)nec, 192, 0, c.s>>>(K0, Ef, Kf, Kc, gf.nx, gf.ny, gf.nz);
+    }
     TOPO_LAUNCH_CHECK(c);
 }
 
