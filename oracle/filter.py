@@ -12,6 +12,13 @@ with the sums over elements inside the domain (the neighbourhood is cut at
 the boundary and S_e normalises over the elements that remain).  Its
 transpose, needed by the chain rule dc/drho = H^T dc/drho~, is
 (H^T g)_i = sum_e w_ei g_e / S_e.
+
+The paper's own filter (Eq. sensitivity filter) smooths the sensitivities
+of the design itself:
+
+    dc^_e = sum_i w_ei rho_i dc_i / (max(gamma, rho_e) S_e),
+
+gamma > 0 small (1e-3 here; the paper leaves its value open).
 """
 from __future__ import annotations
 
@@ -69,6 +76,17 @@ def density_filter_T(g, dims, r) -> np.ndarray:
     for dx, dy, dz, w in offsets(r):
         _shift_accumulate(acc, gs, dx, dy, dz, w)
     return acc.ravel()
+
+
+def sensitivity_filter(rho, dc, dims, r, gamma=1e-3) -> np.ndarray:
+    """Eq. sensitivity filter over the same cut neighbourhoods and sums S_e."""
+    nx, ny, nz = dims
+    rho = np.asarray(rho, dtype=np.float64)
+    t3 = (rho * np.asarray(dc, dtype=np.float64)).reshape(nz, ny, nx)
+    acc = np.zeros_like(t3)
+    for dx, dy, dz, w in offsets(r):
+        _shift_accumulate(acc, t3, dx, dy, dz, w)
+    return acc.ravel() / (np.maximum(gamma, rho) * weight_sums(dims, r))
 
 
 def density_filter_bruteforce(x, dims, r) -> np.ndarray:

@@ -15,6 +15,11 @@ lambda = (l1 + l2)/2, evaluate x_new(lambda), and if the mean filtered
 density mean(H x_new) exceeds volfrac set l1 = lambda, else l2 = lambda.
 The returned design is x_new of the last lambda evaluated, and the change is
 ||x_new - x||_inf (the stopping quantity named after Eq. bisect).
+
+With the paper's sensitivity filter the design is its own physical density:
+oc_update_unfiltered takes already filtered sensitivities, B_e =
+max(-dc_e, 1e-30) / lambda, and bisects on mean(x_new) against volfrac, with
+the same bounds, tolerance and clamps.
 """
 from __future__ import annotations
 
@@ -37,6 +42,27 @@ def oc_update(x, dc, dims, r, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=1e
         cand = x * (num / (lmid * dvt)) ** eta
         xnew = np.maximum(0.0, np.maximum(x - move, np.minimum(1.0, np.minimum(x + move, cand))))
         if density_filter(xnew, dims, r).mean() > volfrac:
+            l1 = lmid
+        else:
+            l2 = lmid
+        steps += 1
+    return xnew, float(np.max(np.abs(xnew - x))), lmid, steps
+
+
+def oc_update_unfiltered(x, dc, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=1e-9):
+    """OC step on a design without density filter (sensitivities filtered by
+    Eq. sensitivity filter beforehand).  Returns (x_new, change, lambda_last,
+    bisection_steps)."""
+    x = np.asarray(x, dtype=np.float64)
+    num = np.maximum(-np.asarray(dc, dtype=np.float64), 1e-30)
+    xnew = x.copy()
+    lmid = 0.5 * (l1 + l2)
+    steps = 0
+    while (l2 - l1) / (l1 + l2) > tol:
+        lmid = 0.5 * (l1 + l2)
+        cand = x * (num / lmid) ** eta
+        xnew = np.maximum(0.0, np.maximum(x - move, np.minimum(1.0, np.minimum(x + move, cand))))
+        if xnew.mean() > volfrac:
             l1 = lmid
         else:
             l2 = lmid

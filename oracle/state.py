@@ -16,9 +16,9 @@ import numpy as np
 
 from .assemble import constrained_system, simp_modulus
 from .element import element_stiffness
-from .filter import density_filter
+from .filter import density_filter, sensitivity_filter
 from .multigrid import homogenized_hierarchy, max_levels, mgpcg_galerkin, vcycle
-from .oc import oc_update
+from .oc import oc_update, oc_update_unfiltered
 from .sensitivity import compliance, element_energy, sensitivity
 from .solve import pcg, solve_dense, solve_sparse_direct
 
@@ -73,3 +73,16 @@ def oc_iteration(dims, x, fixed, f, r, volfrac, move=0.2, nu=0.3, E0=1.0, Emin=1
     C, _, dc = compliance_and_sensitivity(dims, rho, u, f, nu, E0, Emin, penal)
     xn, ch, lam, steps = oc_update(x, dc, dims, r, volfrac, move)
     return dict(C=C, x_new=xn, change=ch, u=u, rho_phys=rho, dc=dc, lam=lam, steps=steps)
+
+
+def oc_iteration_sensitivity_filter(dims, x, fixed, f, r, volfrac, move=0.2, gamma=1e-3, nu=0.3, E0=1.0,
+                                    Emin=1e-9, penal=3.0, tol=1e-10, x0=None):
+    """One loop body of Algorithm 4 as the paper runs it: the design is the
+    physical density, the sensitivities go through Eq. sensitivity filter,
+    then the OC update.  Returns dict(C, x_new, change, u, dc, dc_filtered)."""
+    x = np.asarray(x, dtype=np.float64)
+    u = solve_state(dims, x, fixed, f, nu, E0, Emin, penal, tol=tol, x0=x0)
+    C, _, dc = compliance_and_sensitivity(dims, x, u, f, nu, E0, Emin, penal)
+    dcf = sensitivity_filter(x, dc, dims, r, gamma)
+    xn, ch, lam, steps = oc_update_unfiltered(x, dcf, volfrac, move)
+    return dict(C=C, x_new=xn, change=ch, u=u, dc=dc, dc_filtered=dcf, lam=lam, steps=steps)

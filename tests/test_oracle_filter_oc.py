@@ -121,3 +121,50 @@ def test_oc_fixed_point_when_kkt_holds():
     xn, ch, lam, _ = oc.oc_update(x, dc, dims, r, volfrac=0.4, move=0.2)
     assert lam == pytest.approx(2.5, rel=1e-6)
     assert ch < 1e-6
+
+
+@pytest.mark.parametrize("r", [1.5, 2.5])
+def test_sensitivity_filter_matches_bruteforce(r):
+    """Eq. sensitivity filter against the O(N^2) pair loop applied to rho*dc,
+    divided by max(gamma, rho); densities below gamma exercise the clamp."""
+    dims = (5, 4, 3)
+    rho = synth.uniform_field(dims, 31, 0.0, 1.0)
+    rho[::7] = 1e-4                                   # below gamma = 1e-3
+    dc = -synth.uniform_field(dims, 32, 0.1, 5.0)
+    got = flt.sensitivity_filter(rho, dc, dims, r, gamma=1e-3)
+    ref = flt.density_filter_bruteforce(rho * dc, dims, r) / np.maximum(1e-3, rho)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_sensitivity_filter_constant_fields():
+    """Uniform density and sensitivity are reproduced exactly (up to rounding)."""
+    dims = (6, 5, 4)
+    rho = np.full(120, 0.37)
+    dc = np.full(120, -2.5)
+    got = flt.sensitivity_filter(rho, dc, dims, 2.0)
+    assert np.allclose(got, -2.5, rtol=1e-14, atol=0)
+
+
+def test_oc_unfiltered_bounds_and_volume():
+    dims = (8, 4, 4)
+    vf, move = 0.3, 0.2
+    x = np.full(128, 0.3)
+    dc = -synth.uniform_field(dims, 3, 0.1, 10.0)
+    xn, ch, lam, steps = oc.oc_update_unfiltered(x, dc, vf, move)
+    assert np.all(xn >= 0.0) and np.all(xn <= 1.0)
+    assert np.all(xn >= x - move - 1e-15) and np.all(xn <= x + move + 1e-15)
+    assert abs(xn.mean() - vf) < 1e-6
+    assert ch == pytest.approx(np.abs(xn - x).max())
+
+
+def test_oc_unfiltered_equals_filtered_oc_with_identity_filter():
+    """For r <= 1 the density filter is the identity (only the element itself
+    has positive weight), so the filtered OC step reduces to the unfiltered
+    one."""
+    dims = (6, 4, 4)
+    x = synth.uniform_field(dims, 5, 0.1, 0.9)
+    dc = -synth.uniform_field(dims, 6, 0.1, 10.0)
+    a = oc.oc_update(x, dc, dims, 0.9, 0.45, 0.2)
+    b = oc.oc_update_unfiltered(x, dc, 0.45, 0.2)
+    assert np.abs(a[0] - b[0]).max() < 1e-12
+    assert a[2] == pytest.approx(b[2], rel=1e-12)
