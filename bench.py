@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--coarsening", choices=["density", "modulus", "galerkin"], default="density",
                     help="coarse operators: SIMP of the mean child density (Sec. 4.2.2), mean child modulus, "
                          "or stored Galerkin element matrices")
+    ap.add_argument("--filter", choices=["density", "sensitivity"], default="density",
+                    help="OC loop: density filter (chain rule) or the paper's sensitivity filter")
     ap.add_argument("--oc-loop", action="store_true",
                     help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
@@ -514,7 +516,7 @@ def run_oc_loop(args):
     tol = w.get("rel_tol", 1e-8)
     out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
            "iterations": oc["iters"], "rel_tol": tol, "rmin": oc["rmin"], "move": oc["move"],
-           "volfrac": oc["volfrac"], "coarsening": args.coarsening}
+           "volfrac": oc["volfrac"], "coarsening": args.coarsening, "filter": args.filter}
     runs = {}
     for label, p in (("mixed", prec), ("fp64", TOPO_FP64)):
         g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=COARSENING[args.coarsening]))
@@ -525,10 +527,16 @@ def run_oc_loop(args):
         for it in range(oc["iters"]):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            g.set_density(g.filter(oc["rmin"], x))
-            _, res = g.solve(tol, 20000)
-            C, _ = g.compliance_and_sensitivity(dc)
-            g.oc_update(oc["rmin"], oc["move"], oc["volfrac"], x, dc)
+            if args.filter == "density":
+                g.set_density(g.filter(oc["rmin"], x))
+                _, res = g.solve(tol, 20000)
+                C, _ = g.compliance_and_sensitivity(dc)
+                g.oc_update(oc["rmin"], oc["move"], oc["volfrac"], x, dc)
+            else:   # the paper's loop: design = physical density, filtered sensitivities
+                g.set_density(x)
+                _, res = g.solve(tol, 20000)
+                C, _ = g.compliance_and_sensitivity(dc)
+                g.oc_update_unfiltered(oc["move"], oc["volfrac"], x, g.sensitivity_filter(oc["rmin"], x, dc))
             e1.record()
             torch.cuda.synchronize()
             Cs.append(C)

@@ -150,6 +150,24 @@ topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* o
 topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
                            double* rho_dev_inout, const double* dc_dev, double* change_out);
 
+/* The paper's own filter (Eq. sensitivity filter): the design is the
+ * physical density and its sensitivities are smoothed as
+ *   out_e = sum_i w_ei rho_i dc_i / (max(gamma, rho_e) S_e),
+ * w_ei = max(0, r - |x_i - x_e|) over the neighbourhood cut at the domain
+ * boundary, S_e = sum_i w_ei (the weights of topo_filter).  rho_dev, dc_dev,
+ * out_dev: device, nx*ny*nz FP64; out must not overlap the inputs.
+ * 0 < r <= 6, gamma > 0 (the paper: "a small number"; 1e-3 is typical),
+ * else TOPO_BADARG. */
+topo_status topo_sensitivity_filter(topo_handle h, double r, double gamma, const double* rho_dev,
+                                    const double* dc_dev, double* out_dev);
+
+/* OC update for designs without a density filter (the paper's loop with
+ * the sensitivity filter): as topo_oc_update with dc~ = dc_dev (already
+ * filtered) and dv~ = 1, the bisection matching mean(x_new) = volfrac.
+ * Same arguments, bounds, tolerance and errors as topo_oc_update. */
+topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, double* rho_dev_inout,
+                                      const double* dc_dev, double* change_out);
+
 /* Message of the last failure on this handle ("" if none).  The string is
  * owned by the handle and valid until the next call on it.  With h == NULL
  * returns the message of the last failed topo_create_grid. */

@@ -143,6 +143,24 @@ class TopoGrid:
                                             _ptr(dc, torch.float64, self.ne, "dc"), C.byref(ch)))
         return ch.value
 
+    def sensitivity_filter(self, r: float, rho: torch.Tensor, dc: torch.Tensor, gamma: float = 1e-3,
+                           out: torch.Tensor | None = None):
+        """Eq. sensitivity filter: H(rho dc) / max(gamma, rho)."""
+        out = torch.empty_like(dc) if out is None else out
+        self._check(self.lib.topo_sensitivity_filter(self._h, float(r), float(gamma),
+                                                     _ptr(rho, torch.float64, self.ne, "rho"),
+                                                     _ptr(dc, torch.float64, self.ne, "dc"),
+                                                     _ptr(out, torch.float64, self.ne, "out")))
+        return out
+
+    def oc_update_unfiltered(self, move: float, volfrac: float, x: torch.Tensor, dc: torch.Tensor) -> float:
+        """OC step with already filtered sensitivities and the volume of x itself."""
+        ch = C.c_double(0.0)
+        self._check(self.lib.topo_oc_update_unfiltered(self._h, float(move), float(volfrac),
+                                                       _ptr(x, torch.float64, self.ne, "x"),
+                                                       _ptr(dc, torch.float64, self.ne, "dc"), C.byref(ch)))
+        return ch.value
+
     # -- step-level entry points --------------------------------------------
     def level_dims(self, level: int):
         a, b, c = C.c_int(), C.c_int(), C.c_int()

@@ -605,6 +605,37 @@ topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* o
     return TOPO_OK;
 }
 
+// bisection of Eq. OC on lambda (reading of the paper: l1 = 0, l2 = 1e9,
+// relative tolerance 1e-9) over q = x sqrt(-dc / dv) in dc_work and the
+// bounds in xnew_work / oc_hi; dv null: volume of x itself; writes x and change
+static topo_status oc_bisection(topo_grid* h, double volfrac, double* rho_dev_inout, const double* dv,
+                                double* change_out) {
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
+    const double init[8] = {l1, l2, 0.5 * (l1 + l2), (l2 - l1) / (l1 + l2) > tol ? 0.0 : 1.0, 0.0, 0.5 * (l1 + l2),
+                            0.0, 0.0};
+    CK(h, cudaMemcpyAsync(h->lam, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    double state[8];
+    for (int batch = 0; batch < 25; ++batch) {
+        for (int k = 0; k < 16; ++k) {
+            oc_bisect_step(c, g.ne, h->xnew_work, h->oc_hi, h->dc_work, dv, h->partials, h->lam);
+            oc_bisect_finalize(c, h->partials, h->lam, volfrac * (double)g.ne, tol);
+        }
+        CK(h, cudaMemcpyAsync(state, h->lam, sizeof(state), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (state[3] != 0.0) break;
+    }
+    if (state[3] == 0.0) return fail(h, TOPO_MAXITER, "bisection did not converge");
+    oc_write(c, g.ne, rho_dev_inout, h->xnew_work, h->oc_hi, h->dc_work, h->lam, h->partials, h->dtmp);
+    if (change_out) {
+        CK(h, cudaMemcpyAsync(change_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
 topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac, double* rho_dev_inout,
                            const double* dc_dev, double* change_out) {
     topo_status s = check_handle(h);
@@ -620,26 +651,34 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
     filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dc_work, 1, nullptr);
     // q over dc_work, lower bounds in xnew_work, upper bounds in oc_hi
     oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->xnew_work, h->oc_hi);
-    const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
-    const double init[8] = {l1, l2, 0.5 * (l1 + l2), (l2 - l1) / (l1 + l2) > tol ? 0.0 : 1.0, 0.0, 0.5 * (l1 + l2),
-                            0.0, 0.0};
-    CK(h, cudaMemcpyAsync(h->lam, init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-    double state[8];
-    for (int batch = 0; batch < 25; ++batch) {
-        for (int k = 0; k < 16; ++k) {
-            oc_bisect_step(c, g.ne, h->xnew_work, h->oc_hi, h->dc_work, h->dv_cache, h->partials, h->lam);
-            oc_bisect_finalize(c, h->partials, h->lam, volfrac * (double)g.ne, tol);
-        }
-        CK(h, cudaMemcpyAsync(state, h->lam, sizeof(state), cudaMemcpyDeviceToHost, h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
-        if (state[3] != 0.0) break;
-    }
-    if (state[3] == 0.0) return fail(h, TOPO_MAXITER, "bisection did not converge");
-    oc_write(c, g.ne, rho_dev_inout, h->xnew_work, h->oc_hi, h->dc_work, h->lam, h->partials, h->dtmp);
-    if (change_out) {
-        CK(h, cudaMemcpyAsync(change_out, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));
-    }
+    return oc_bisection(h, volfrac, rho_dev_inout, h->dv_cache, change_out);
+}
+
+topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, double* rho_dev_inout,
+                                      const double* dc_dev, double* change_out) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev_inout || !dc_dev) return fail(h, TOPO_BADARG, "NULL pointer");
+    if (!(move > 0.0 && move <= 1.0) || !(volfrac > 0.0 && volfrac < 1.0))
+        return fail(h, TOPO_BADARG, "move must be in (0,1], volfrac in (0,1)");
+    const Ctx c = h->ctx();
+    const Geom& g = h->lev[0].g;
+    CK(h, cudaMemcpyAsync(h->dc_work, dc_dev, sizeof(double) * g.ne, cudaMemcpyDeviceToDevice, h->stream));
+    oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, nullptr, move, h->xnew_work, h->oc_hi);
+    return oc_bisection(h, volfrac, rho_dev_inout, nullptr, change_out);
+}
+
+topo_status topo_sensitivity_filter(topo_handle h, double r, double gamma, const double* rho_dev,
+                                    const double* dc_dev, double* out_dev) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev || !dc_dev || !out_dev || out_dev == rho_dev || out_dev == dc_dev)
+        return fail(h, TOPO_BADARG, "bad pointers");
+    if (!(gamma > 0.0)) return fail(h, TOPO_BADARG, "gamma must be positive");
+    s = prepare_filter(h, r);
+    if (s != TOPO_OK) return s;
+    sensitivity_filter(h->ctx(), h->lev[0].g, h->offs, h->wts, h->noffs, rho_dev, dc_dev, gamma, h->xnew_work,
+                       out_dev);
     CK(h, cudaGetLastError());
     return TOPO_OK;
 }

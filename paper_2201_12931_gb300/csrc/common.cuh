@@ -231,7 +231,12 @@ void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* 
                    double* out, int mode, const double* S);
 void divide(const Ctx& c, long long n, const double* a, const double* b, double* out);
 // q = x sqrt(max(-dc~, 1e-30) / dv~)
-// q = x sqrt(max(-dc~,1e-30)/dv~) in place over dc~; lo / hi: move-limit bounds
+// Eq. sensitivity filter: out = H(rho dc) / max(gamma, rho), tmp: work array
+void sensitivity_filter(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs,
+                        const double* rho, const double* dc, double gamma, double* tmp, double* out);
+// q = x sqrt(max(-dc~,1e-30)/dv~) in place over dc~ (dv~ null: 1); lo / hi:
+// move-limit bounds.  The bisection steps take dv~ null for the volume of x
+// itself (no density filter).
 void oc_prepare(const Ctx& c, long long ne, const double* x, double* dct_q, const double* dv, double move, double* lo,
                 double* hi);
 void oc_bisect_step(const Ctx& c, long long ne, const double* lo, const double* hi, const double* num,

@@ -84,6 +84,19 @@ __global__ void __launch_bounds__(256) k_filter(const int4* __restrict__ offs, c
     }
 }
 
+// Eq. sensitivity filter: t = rho dc before the normalised filter, and the
+// division by max(gamma, rho_e) after it
+__global__ void k_mul(long long n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = a[e] * b[e];
+}
+__global__ void k_div_max(long long n, double* __restrict__ out, const double* __restrict__ rho, double gamma) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    out[e] = out[e] / fmax(gamma, rho[e]);
+}
+
 __global__ void k_divide(long long n, const double* __restrict__ a, const double* __restrict__ b,
                          double* __restrict__ out) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -100,7 +113,7 @@ __global__ void k_oc_prepare(long long ne, const double* __restrict__ x, double*
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= ne) return;
     const double xe = x[e];
-    dct_q[e] = xe * sqrt(fmax(-dct_q[e], 1e-30) / dv[e]);
+    dct_q[e] = xe * sqrt(fmax(-dct_q[e], 1e-30) / (dv ? dv[e] : 1.0));
     lo[e] = fmax(0.0, xe - move);
     hi[e] = fmin(1.0, xe + move);
 }
@@ -126,8 +139,15 @@ __global__ void __launch_bounds__(256) k_oc_step(long long ne, const double* __r
     }
     const double sl = rsqrt(lam[2]);
     double s = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x)
-        s += dv[e] * oc_candidate(num[e], sl, lo[e], hi[e]);
+    if (dv) {
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
+             e += (long long)gridDim.x * blockDim.x)
+            s += dv[e] * oc_candidate(num[e], sl, lo[e], hi[e]);
+    } else {   // no density filter: the volume of the design itself
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
+             e += (long long)gridDim.x * blockDim.x)
+            s += oc_candidate(num[e], sl, lo[e], hi[e]);
+    }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -190,6 +210,15 @@ void filter_launch(const Ctx& c, const Geom& g, const int4* offs, const double* 
 
 void divide(const Ctx& c, long long n, const double* a, const double* b, double* out) {
     k_divide<<<grid_for(n, 256), 256, 0, c.s>>>(n, a, b, out);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void sensitivity_filter(const Ctx& c, const Geom& g, const int4* offs, const double* wts, int noffs,
+                        const double* rho, const double* dc, double gamma, double* tmp, double* out) {
+    k_mul<<<grid_for(g.ne, 256), 256, 0, c.s>>>(g.ne, rho, dc, tmp);
+    TOPO_LAUNCH_CHECK(c);
+    filter_launch(c, g, offs, wts, noffs, tmp, out, 0, nullptr);
+    k_div_max<<<grid_for(g.ne, 256), 256, 0, c.s>>>(g.ne, out, rho, gamma);
     TOPO_LAUNCH_CHECK(c);
 }
 

@@ -160,3 +160,31 @@ def test_oc_update_given_dc(dims, r):
     xo, cho, lam, steps = ooc.oc_update(x, dc, dims, r, 0.35, 0.2)
     assert np.abs(n(xg) - xo).max() < 1e-7
     assert abs(ch - cho) < 1e-7
+
+
+@pytest.mark.parametrize("r", [1.5, 2.5, 3.0])
+@pytest.mark.parametrize("dims", [(7, 5, 3), (33, 17, 9)])
+def test_sensitivity_filter(r, dims):
+    """Eq. sensitivity filter against the oracle (FP64, 1e-13), densities
+    below gamma included."""
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    g = TopoGrid(dims, Params(levels=1))
+    rho = synth.uniform_field(dims, 61, 0.0, 1.0)
+    rho[::5] = 2e-4
+    dc = -synth.uniform_field(dims, 62, 0.01, 5.0)
+    got = n(g.sensitivity_filter(r, t(rho), t(dc), gamma=1e-3))
+    ref = oflt.sensitivity_filter(rho, dc, dims, r, 1e-3)
+    assert rel_max(got, ref) < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(8, 4, 4), (40, 24, 16)])
+def test_oc_update_unfiltered_given_dc(dims):
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    g = TopoGrid(dims, Params(levels=1))
+    x = synth.uniform_field(dims, 53, 0.1, 0.6)
+    dc = -synth.uniform_field(dims, 54, 0.01, 5.0)
+    xg = t(x)
+    ch = g.oc_update_unfiltered(0.2, 0.35, xg, t(dc))
+    xo, cho, lam, steps = ooc.oc_update_unfiltered(x, dc, 0.35, 0.2)
+    assert np.abs(n(xg) - xo).max() < 1e-7
+    assert abs(ch - cho) < 1e-7
