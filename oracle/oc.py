@@ -49,12 +49,17 @@ def oc_update(x, dc, dims, r, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=1e
     return xnew, float(np.max(np.abs(xnew - x))), lmid, steps
 
 
-def oc_update_unfiltered(x, dc, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=1e-9):
+def oc_update_unfiltered(x, dc, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=1e-9, passive=None):
     """OC step on a design without density filter (sensitivities filtered by
-    Eq. sensitivity filter beforehand).  Returns (x_new, change, lambda_last,
-    bisection_steps)."""
+    Eq. sensitivity filter beforehand).  passive (optional, per element):
+    0 active, 1 passive solid (x = 1), 2 passive void (x = 0); passive
+    elements take their value and the volume fraction is that of the active
+    elements (Sec. 5, Examples 2 and 4).  Returns (x_new, change,
+    lambda_last, bisection_steps)."""
     x = np.asarray(x, dtype=np.float64)
     num = np.maximum(-np.asarray(dc, dtype=np.float64), 1e-30)
+    pas = np.zeros(x.size, dtype=np.uint8) if passive is None else np.asarray(passive, dtype=np.uint8)
+    active = pas == 0
     xnew = x.copy()
     lmid = 0.5 * (l1 + l2)
     steps = 0
@@ -62,7 +67,9 @@ def oc_update_unfiltered(x, dc, volfrac, move=0.2, eta=0.5, l1=0.0, l2=1e9, tol=
         lmid = 0.5 * (l1 + l2)
         cand = x * (num / lmid) ** eta
         xnew = np.maximum(0.0, np.maximum(x - move, np.minimum(1.0, np.minimum(x + move, cand))))
-        if xnew.mean() > volfrac:
+        xnew[pas == 1] = 1.0
+        xnew[pas == 2] = 0.0
+        if xnew[active].mean() > volfrac:
             l1 = lmid
         else:
             l2 = lmid

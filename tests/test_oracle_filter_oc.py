@@ -168,3 +168,19 @@ def test_oc_unfiltered_equals_filtered_oc_with_identity_filter():
     b = oc.oc_update_unfiltered(x, dc, 0.45, 0.2)
     assert np.abs(a[0] - b[0]).max() < 1e-12
     assert a[2] == pytest.approx(b[2], rel=1e-12)
+
+
+def test_oc_unfiltered_passive_elements():
+    dims = (8, 4, 4)
+    x = np.full(128, 0.3)
+    passive = np.zeros(128, dtype=np.uint8)
+    passive[:16] = 1                 # solid slab
+    passive[60:70] = 2               # void slot
+    x[passive == 1], x[passive == 2] = 1.0, 0.0
+    dc = -synth.uniform_field(dims, 3, 0.1, 10.0)
+    xn, ch, lam, steps = oc.oc_update_unfiltered(x, dc, 0.3, 0.2, passive=passive)
+    assert np.all(xn[passive == 1] == 1.0) and np.all(xn[passive == 2] == 0.0)
+    assert abs(xn[passive == 0].mean() - 0.3) < 1e-6
+    same = oc.oc_update_unfiltered(x, dc, 0.3, 0.2, passive=np.zeros(128, dtype=np.uint8))
+    plain = oc.oc_update_unfiltered(x, dc, 0.3, 0.2)
+    assert np.array_equal(same[0], plain[0])
