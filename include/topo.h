@@ -164,9 +164,31 @@ topo_status topo_sensitivity_filter(topo_handle h, double r, double gamma, const
 /* OC update for designs without a density filter (the paper's loop with
  * the sensitivity filter): as topo_oc_update with dc~ = dc_dev (already
  * filtered) and dv~ = 1, the bisection matching mean(x_new) = volfrac.
- * Same arguments, bounds, tolerance and errors as topo_oc_update. */
-topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, double* rho_dev_inout,
-                                      const double* dc_dev, double* change_out);
+ * passive_dev (device, nx*ny*nz bytes, may be NULL): 0 active element,
+ * 1 passive solid (x_new = 1), 2 passive void (x_new = 0) -- the
+ * non-design regions of Sec. 5, Examples 2 and 4; volfrac is then the
+ * volume fraction of the active elements (TOPO_BADARG if there are none).
+ * Other arguments, bounds, tolerance and errors as topo_oc_update. */
+topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, const uint8_t* passive_dev,
+                                      double* rho_dev_inout, const double* dc_dev, double* change_out);
+
+/* Design-dependent self-weight load (Sec. 5, Example 4: gravity load
+ * proportional to the material present): element e carries the weight
+ * w rho_e in -z, lumped 1/8 to each corner (the consistent load of a
+ * constant body force on the trilinear brick):
+ *   f_out = f_ext + sum_e rho_e g_e,  g_e = -(w/8) e_z at the 8 corners.
+ * rho_dev: device, nx*ny*nz FP64; f_ext_dev: device 3*nodes FP64 or NULL
+ * (zero); f_out_dev: device 3*nodes FP64, not overlapping f_ext.  No
+ * Dirichlet masking here: pass f_out to topo_set_bc_loads. */
+topo_status topo_gravity_load(topo_handle h, double w, const double* rho_dev, const double* f_ext_dev,
+                              double* f_out_dev);
+
+/* Adds the load term of the compliance sensitivity with the self-weight
+ * load of topo_gravity_load: dc_e += 2 u_e^T g_e = -(w/4) * (sum of u_z at
+ * the 8 corners of e), u the handle's current solution (from
+ * topo_solve_state).  Call after topo_compliance_and_sensitivity, which
+ * gives the stiffness term.  dc_dev_inout: device, nx*ny*nz FP64. */
+topo_status topo_gravity_sensitivity(topo_handle h, double w, double* dc_dev_inout);
 
 /* Message of the last failure on this handle ("" if none).  The string is
  * owned by the handle and valid until the next call on it.  With h == NULL

@@ -43,7 +43,9 @@ _SIGS = {
     "topo_filter": ([H, C.c_double, P, P, C.c_int], C.c_int),
     "topo_oc_update": ([H, C.c_double, C.c_double, C.c_double, P, P, C.POINTER(C.c_double)], C.c_int),
     "topo_sensitivity_filter": ([H, C.c_double, C.c_double, P, P, P], C.c_int),
-    "topo_oc_update_unfiltered": ([H, C.c_double, C.c_double, P, P, C.POINTER(C.c_double)], C.c_int),
+    "topo_oc_update_unfiltered": ([H, C.c_double, C.c_double, P, P, P, C.POINTER(C.c_double)], C.c_int),
+    "topo_gravity_load": ([H, C.c_double, P, P, P], C.c_int),
+    "topo_gravity_sensitivity": ([H, C.c_double, P], C.c_int),
     "topo_last_error": ([H], C.c_char_p),
     "topo_level_dims": ([H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "topo_apply_operator": ([H, C.c_int, C.c_int, P, P], C.c_int),

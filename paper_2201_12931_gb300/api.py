@@ -153,13 +153,30 @@ class TopoGrid:
                                                      _ptr(out, torch.float64, self.ne, "out")))
         return out
 
-    def oc_update_unfiltered(self, move: float, volfrac: float, x: torch.Tensor, dc: torch.Tensor) -> float:
-        """OC step with already filtered sensitivities and the volume of x itself."""
+    def oc_update_unfiltered(self, move: float, volfrac: float, x: torch.Tensor, dc: torch.Tensor,
+                             passive: torch.Tensor | None = None) -> float:
+        """OC step with already filtered sensitivities and the volume of x itself;
+        passive (uint8 per element): 0 active, 1 solid, 2 void."""
         ch = C.c_double(0.0)
-        self._check(self.lib.topo_oc_update_unfiltered(self._h, float(move), float(volfrac),
+        pp = None if passive is None else _ptr(passive, torch.uint8, self.ne, "passive")
+        self._check(self.lib.topo_oc_update_unfiltered(self._h, float(move), float(volfrac), pp,
                                                        _ptr(x, torch.float64, self.ne, "x"),
                                                        _ptr(dc, torch.float64, self.ne, "dc"), C.byref(ch)))
         return ch.value
+
+    def gravity_load(self, w: float, rho: torch.Tensor, f_ext: torch.Tensor | None = None,
+                     out: torch.Tensor | None = None):
+        """f_ext + self-weight of density rho (w per unit-density element, -z)."""
+        out = torch.empty(3 * self.nn, dtype=torch.float64, device=rho.device) if out is None else out
+        fe = None if f_ext is None else _ptr(f_ext, torch.float64, 3 * self.nn, "f_ext")
+        self._check(self.lib.topo_gravity_load(self._h, float(w), _ptr(rho, torch.float64, self.ne, "rho"), fe,
+                                               _ptr(out, torch.float64, 3 * self.nn, "out")))
+        return out
+
+    def gravity_sensitivity(self, w: float, dc: torch.Tensor):
+        """dc += load term of the self-weight sensitivity (in place)."""
+        self._check(self.lib.topo_gravity_sensitivity(self._h, float(w), _ptr(dc, torch.float64, self.ne, "dc")))
+        return dc
 
     # -- step-level entry points --------------------------------------------
     def level_dims(self, level: int):

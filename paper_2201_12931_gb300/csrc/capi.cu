@@ -166,7 +166,7 @@ void free_all(topo_grid* h) {
     F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
     F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
     F(h->K0d); F(h->K0f);
-    F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->G64); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
+    F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->G64); F(h->oc_dv); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
     F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
     if (h->host_sc) cudaFreeHost(h->host_sc);
     delete h->mk64;
@@ -609,7 +609,7 @@ topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* o
 // relative tolerance 1e-9) over q = x sqrt(-dc / dv) in dc_work and the
 // bounds in xnew_work / oc_hi; dv null: volume of x itself; writes x and change
 static topo_status oc_bisection(topo_grid* h, double volfrac, double* rho_dev_inout, const double* dv,
-                                double* change_out) {
+                                double* change_out, double n_volume) {
     const Ctx c = h->ctx();
     const Geom& g = h->lev[0].g;
     const double l1 = 0.0, l2 = 1e9, tol = 1e-9;
@@ -620,7 +620,7 @@ static topo_status oc_bisection(topo_grid* h, double volfrac, double* rho_dev_in
     for (int batch = 0; batch < 25; ++batch) {
         for (int k = 0; k < 16; ++k) {
             oc_bisect_step(c, g.ne, h->xnew_work, h->oc_hi, h->dc_work, dv, h->partials, h->lam);
-            oc_bisect_finalize(c, h->partials, h->lam, volfrac * (double)g.ne, tol);
+            oc_bisect_finalize(c, h->partials, h->lam, volfrac * n_volume, tol);
         }
         CK(h, cudaMemcpyAsync(state, h->lam, sizeof(state), cudaMemcpyDeviceToHost, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -651,11 +651,11 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
     filter_launch(c, g, h->offs, h->wts, h->noffs, h->xnew_work, h->dc_work, 1, nullptr);
     // q over dc_work, lower bounds in xnew_work, upper bounds in oc_hi
     oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, h->dv_cache, move, h->xnew_work, h->oc_hi);
-    return oc_bisection(h, volfrac, rho_dev_inout, h->dv_cache, change_out);
+    return oc_bisection(h, volfrac, rho_dev_inout, h->dv_cache, change_out, (double)g.ne);
 }
 
-topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, double* rho_dev_inout,
-                                      const double* dc_dev, double* change_out) {
+topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac, const uint8_t* passive_dev,
+                                      double* rho_dev_inout, const double* dc_dev, double* change_out) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
     if (!rho_dev_inout || !dc_dev) return fail(h, TOPO_BADARG, "NULL pointer");
@@ -664,8 +664,38 @@ topo_status topo_oc_update_unfiltered(topo_handle h, double move, double volfrac
     const Ctx c = h->ctx();
     const Geom& g = h->lev[0].g;
     CK(h, cudaMemcpyAsync(h->dc_work, dc_dev, sizeof(double) * g.ne, cudaMemcpyDeviceToDevice, h->stream));
-    oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, nullptr, move, h->xnew_work, h->oc_hi);
-    return oc_bisection(h, volfrac, rho_dev_inout, nullptr, change_out);
+    if (!passive_dev) {
+        oc_prepare(c, g.ne, rho_dev_inout, h->dc_work, nullptr, move, h->xnew_work, h->oc_hi);
+        return oc_bisection(h, volfrac, rho_dev_inout, nullptr, change_out, (double)g.ne);
+    }
+    if (!h->oc_dv) ALLOC(h, h->oc_dv, g.ne);
+    oc_prepare_passive(c, g.ne, rho_dev_inout, h->dc_work, passive_dev, move, h->xnew_work, h->oc_hi, h->oc_dv);
+    dot_partials<double, double>(c, g.ne, h->oc_dv, h->oc_dv, h->partials);   // number of active elements
+    reduce_to(c, h->partials, kRedBlocks, h->dtmp);
+    double n_active = 0.0;
+    CK(h, cudaMemcpyAsync(&n_active, h->dtmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (!(n_active > 0.0)) return fail(h, TOPO_BADARG, "no active elements");
+    return oc_bisection(h, volfrac, rho_dev_inout, h->oc_dv, change_out, n_active);
+}
+
+topo_status topo_gravity_load(topo_handle h, double w, const double* rho_dev, const double* f_ext_dev,
+                              double* f_out_dev) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev || !f_out_dev || f_out_dev == f_ext_dev) return fail(h, TOPO_BADARG, "bad pointers");
+    gravity_load(h->ctx(), h->lev[0].g, rho_dev, f_ext_dev, f_out_dev, w);
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
+}
+
+topo_status topo_gravity_sensitivity(topo_handle h, double w, double* dc_dev_inout) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!dc_dev_inout) return fail(h, TOPO_BADARG, "NULL pointer");
+    gravity_sensitivity(h->ctx(), h->lev[0].g, h->x, dc_dev_inout, w);
+    CK(h, cudaGetLastError());
+    return TOPO_OK;
 }
 
 topo_status topo_sensitivity_filter(topo_handle h, double r, double gamma, const double* rho_dev,

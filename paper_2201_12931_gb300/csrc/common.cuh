@@ -106,6 +106,7 @@ struct topo_grid {
     double* xnew_work = nullptr;
     double* oc_hi = nullptr;        // OC upper move-limit bounds
     double* G64 = nullptr;          // Galerkin child matrices P_o^T K0 P_o (homogenize = 2)
+    double* oc_dv = nullptr;        // active-element indicator of a passive OC step (lazy)
     double* S_cache = nullptr;      // filter weight sums S_e for S_radius
     double* dv_cache = nullptr;     // H^T 1 for S_radius
     int4* offs = nullptr;           // filter offsets for S_radius
@@ -239,6 +240,14 @@ void sensitivity_filter(const Ctx& c, const Geom& g, const int4* offs, const dou
 // itself (no density filter).
 void oc_prepare(const Ctx& c, long long ne, const double* x, double* dct_q, const double* dv, double move, double* lo,
                 double* hi);
+// passive elements (0 active, 1 solid, 2 void): lo = hi = 1 / 0, q = 0,
+// dv = 0; active: q = x sqrt(max(-dc, 1e-30)), move-limit bounds, dv = 1
+void oc_prepare_passive(const Ctx& c, long long ne, const double* x, double* dct_q, const uint8_t* passive,
+                        double move, double* lo, double* hi, double* dv);
+// self-weight load f_out = f_ext (null: 0) - (w/8) sum of rho over the elements at each node, in z
+void gravity_load(const Ctx& c, const Geom& g, const double* rho, const double* f_ext, double* f_out, double w);
+// dc_e += -(w/4) sum of u_z over the corners of e
+void gravity_sensitivity(const Ctx& c, const Geom& g, const double* u, double* dc, double w);
 void oc_bisect_step(const Ctx& c, long long ne, const double* lo, const double* hi, const double* num,
                     const double* dv, double* partials, double* lam_state);
 void oc_bisect_finalize(const Ctx& c, const double* partials, double* lam_state, double volfrac_ne,

@@ -118,6 +118,67 @@ __global__ void k_oc_prepare(long long ne, const double* __restrict__ x, double*
     hi[e] = fmin(1.0, xe + move);
 }
 
+// passive elements (0 active, 1 solid, 2 void) take x = 1 / 0 through
+// lo = hi and carry no volume (dv = 0); active elements: dv = 1
+__global__ void k_oc_prepare_passive(long long ne, const double* __restrict__ x, double* dc_q,
+                                     const uint8_t* __restrict__ passive, double move, double* __restrict__ lo,
+                                     double* __restrict__ hi, double* __restrict__ dv) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const unsigned p = passive[e];
+    if (p != 0) {
+        const double v = p == 1 ? 1.0 : 0.0;
+        dc_q[e] = 0.0;
+        lo[e] = hi[e] = v;
+        dv[e] = 0.0;
+        return;
+    }
+    const double xe = x[e];
+    dc_q[e] = xe * sqrt(fmax(-dc_q[e], 1e-30));
+    lo[e] = fmax(0.0, xe - move);
+    hi[e] = fmin(1.0, xe + move);
+    dv[e] = 1.0;
+}
+
+// Self-weight (design-dependent) load: f_out = f_ext + sum_e rho_e g_e with
+// g_e = -(w/8) e_z at the 8 corners of e; one thread per node
+__global__ void k_gravity_load(const double* __restrict__ rho, const double* __restrict__ f_ext,
+                               double* __restrict__ f_out, double w, int nx, int ny, int nz) {
+    const int NX = nx + 1, NY = ny + 1;
+    const long long nn = (long long)NX * NY * (nz + 1);
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((long long)NX * NY));
+    double s = 0.0;
+    for (int dz = -1; dz <= 0; ++dz)
+        for (int dy = -1; dy <= 0; ++dy)
+            for (int dx = -1; dx <= 0; ++dx) {
+                const int ex = i + dx, ey = j + dy, ez = k + dz;
+                if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || ez < 0 || ez >= nz) continue;
+                s += rho[ex + (long long)nx * (ey + (long long)ny * ez)];
+            }
+    f_out[3 * n + 0] = f_ext ? f_ext[3 * n + 0] : 0.0;
+    f_out[3 * n + 1] = f_ext ? f_ext[3 * n + 1] : 0.0;
+    f_out[3 * n + 2] = (f_ext ? f_ext[3 * n + 2] : 0.0) - 0.125 * w * s;
+}
+
+// dc_e += 2 u_e^T g_e = -(w/4) sum of u_z over the 8 corners of e
+__global__ void k_gravity_sens(const double* __restrict__ u, double* __restrict__ dc, double w, int nx, int ny,
+                               int nz) {
+    const long long ne = (long long)nx * ny * nz;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int NX = nx + 1, NY = ny + 1;
+    const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
+        s += u[3 * nd + 2];
+    }
+    dc[e] += -0.25 * w * s;
+}
+
 // lam state: [0] l1, [1] l2, [2] lmid (next to evaluate), [3] done, [4] steps, [5] last lmid
 // candidate min(hi, max(lo, q s)) with s = lambda^(-1/2); the three values are
 // non-negative, so the clamps compare their IEEE bit patterns as integers
@@ -225,6 +286,22 @@ void sensitivity_filter(const Ctx& c, const Geom& g, const int4* offs, const dou
 void oc_prepare(const Ctx& c, long long ne, const double* x, double* dct_q, const double* dv, double move, double* lo,
                 double* hi) {
     k_oc_prepare<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, x, dct_q, dv, move, lo, hi);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void oc_prepare_passive(const Ctx& c, long long ne, const double* x, double* dct_q, const uint8_t* passive,
+                        double move, double* lo, double* hi, double* dv) {
+    k_oc_prepare_passive<<<grid_for(ne, 256), 256, 0, c.s>>>(ne, x, dct_q, passive, move, lo, hi, dv);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void gravity_load(const Ctx& c, const Geom& g, const double* rho, const double* f_ext, double* f_out, double w) {
+    k_gravity_load<<<grid_for(g.nn, 256), 256, 0, c.s>>>(rho, f_ext, f_out, w, g.nx, g.ny, g.nz);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void gravity_sensitivity(const Ctx& c, const Geom& g, const double* u, double* dc, double w) {
+    k_gravity_sens<<<grid_for(g.ne, 256), 256, 0, c.s>>>(u, dc, w, g.nx, g.ny, g.nz);
     TOPO_LAUNCH_CHECK(c);
 }
 

@@ -150,6 +150,36 @@ def mbb_half(dims) -> Problem:
     return Problem(tuple(dims), fixed, f, name=f"mbb_{nx}x{ny}x{nz}")
 
 
+def arch_bridge(dims, deck_layers, slot_halfwidth, q=1.0) -> Problem:
+    """Bridge-like domain with non-design regions (Sec. 5, Example 2; the
+    geometry is only in the paper's figures, so this is a stand-in): the top
+    `deck_layers` element layers are passive solid, a slot of the elements within slot_halfwidth of
+    elements around mid-span below the deck is passive void; simple supports
+    at the four bottom corners (u fixed at (0,0,0); u_y, u_z at (nx,0,0);
+    u_z at (0,ny,0) and (nx,ny,0)); uniform pressure q on the top surface,
+    consistent nodal loads q/4 per adjacent unit face.  info["passive"]:
+    uint8 per element, 0 active, 1 solid, 2 void."""
+    nx, ny, nz = dims
+    nn = n_nodes(dims)
+    fixed = np.zeros(3 * nn, dtype=np.uint8)
+    fixed[3 * node_index(dims, 0, 0, 0) + np.arange(3)] = 1
+    fixed[3 * node_index(dims, nx, 0, 0) + 1] = 1
+    fixed[3 * node_index(dims, nx, 0, 0) + 2] = 1
+    fixed[3 * node_index(dims, 0, ny, 0) + 2] = 1
+    fixed[3 * node_index(dims, nx, ny, 0) + 2] = 1
+    f = np.zeros(3 * nn)
+    wx, wy = _line_weights(nx + 1), _line_weights(ny + 1)
+    jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    top = node_index(dims, ii.ravel(), jj.ravel(), nz)
+    f[3 * top + 2] = -q * np.outer(wy, wx).ravel()
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    passive = np.zeros(nx * ny * nz, dtype=np.uint8)
+    passive[(k >= nz - deck_layers).ravel()] = 1
+    slot = (np.abs(i + 0.5 - nx / 2) <= slot_halfwidth) & (k < nz - deck_layers)
+    passive[slot.ravel()] = 2
+    return Problem(tuple(dims), fixed, f, name=f"arch_bridge_{nx}x{ny}x{nz}", info=dict(passive=passive))
+
+
 # ---------------------------------------------------------------------------
 # Named workloads.  Each one records the grid, material, solver levels and the
 # recipe of its density field.  Density recipes that need the density filter
@@ -187,6 +217,20 @@ WORKLOADS = {
         dims=(128, 64, 64), problem="cantilever", levels=5, precision="mixed",
         density=dict(kind="const", value=0.12), rel_tol=1e-8,
         oc=dict(iters=49, rmin=1.5, move=0.2, volfrac=0.12)),
+    # bridge stand-ins with non-design regions (Sec. 5, Examples 2 and 4):
+    # 140 x 10 x 20 domain at 448 x 32 x 64, deck 1.5 (5 layers) passive
+    # solid, void slot of the 4 elements within 1.5 of mid-span, volume fraction 0.14
+    # of the active region; the gravity variant adds the self-weight load
+    "arch_bridge_448x32x64_passive": dict(
+        dims=(448, 32, 64), problem="arch_bridge", levels=5, precision="mixed",
+        density=dict(kind="const", value=0.14), rel_tol=1e-8,
+        bridge=dict(deck_layers=5, slot_halfwidth=1.5, q=1.0, weight=0.0),
+        oc=dict(iters=30, rmin=1.5, move=0.2, volfrac=0.14)),
+    "arch_bridge_448x32x64_gravity": dict(
+        dims=(448, 32, 64), problem="arch_bridge", levels=5, precision="mixed",
+        density=dict(kind="const", value=0.14), rel_tol=1e-8,
+        bridge=dict(deck_layers=5, slot_halfwidth=1.5, q=1.0, weight=0.05),
+        oc=dict(iters=30, rmin=1.5, move=0.2, volfrac=0.14)),
     "cantilever_768x384x384_mixed": dict(
         dims=(768, 384, 384), problem="cantilever", levels=7, precision="mixed",
         density=dict(kind="uniform_filtered_clipped", seed=3, lo=0.0, hi=1.0,
@@ -198,6 +242,11 @@ WORKLOADS = {
 def make_problem(name: str, dims=None) -> Problem:
     w = WORKLOADS[name]
     dims = tuple(dims or w["dims"])
+    if w["problem"] == "arch_bridge":
+        b = w["bridge"]
+        p = arch_bridge(dims, b["deck_layers"], b["slot_halfwidth"], b["q"])
+        p.info.update(w)
+        return p
     p = cantilever(dims) if w["problem"] == "cantilever" else mbb_half(dims)
     p.info = dict(w)
     return p
@@ -210,5 +259,9 @@ def raw_density(name: str, dims=None) -> np.ndarray:
     d = w["density"]
     nel = dims[0] * dims[1] * dims[2]
     if d["kind"] == "const":
-        return np.full(nel, d["value"])
+        x = np.full(nel, d["value"])
+        if w["problem"] == "arch_bridge":   # passive regions start at their values
+            pas = make_problem(name, dims).info["passive"]
+            x[pas == 1], x[pas == 2] = 1.0, 0.0
+        return x
     return uniform_field(dims, d["seed"], d["lo"], d["hi"])

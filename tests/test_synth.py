@@ -3,6 +3,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 import synth
 
@@ -53,3 +54,14 @@ def test_cantilever_fixed_at_matches_mask():
     pb = synth.cantilever(dims)
     dofs = np.arange(pb.fixed.size)
     assert np.array_equal(synth.cantilever_fixed_at(dims, dofs), pb.fixed)
+
+
+def test_arch_bridge_regions_and_loads():
+    dims = (32, 8, 16)
+    pb = synth.arch_bridge(dims, deck_layers=2, slot_halfwidth=1.5, q=2.0)
+    pas = pb.info["passive"].reshape(16, 8, 32)
+    assert np.all(pas[14:] == 1)
+    assert np.all(pas[:14, :, 15:17] == 2) and np.all(pas[:14, :, 14] == 2) and np.all(pas[:14, :, 17] == 2)
+    assert np.all(pas[:14, :, :14] == 0) and np.all(pas[:14, :, 18:] == 0)
+    assert pb.f[2::3].sum() == pytest.approx(-2.0 * 32 * 8)      # resultant of the pressure
+    assert pb.fixed.sum() == 3 + 2 + 1 + 1
