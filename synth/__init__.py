@@ -153,20 +153,21 @@ def mbb_half(dims) -> Problem:
 def arch_bridge(dims, deck_layers, slot_halfwidth, q=1.0) -> Problem:
     """Bridge-like domain with non-design regions (Sec. 5, Example 2; the
     geometry is only in the paper's figures, so this is a stand-in): the top
-    `deck_layers` element layers are passive solid, a slot of the elements within slot_halfwidth of
-    elements around mid-span below the deck is passive void; simple supports
-    at the four bottom corners (u fixed at (0,0,0); u_y, u_z at (nx,0,0);
-    u_z at (0,ny,0) and (nx,ny,0)); uniform pressure q on the top surface,
-    consistent nodal loads q/4 per adjacent unit face.  info["passive"]:
-    uint8 per element, 0 active, 1 solid, 2 void."""
+    `deck_layers` element layers are passive solid; the elements within
+    slot_halfwidth of mid-span in the lower half of the height are passive
+    void; supports on the two bottom end lines (u_z = 0 on (0, j, 0) and
+    (nx, j, 0), u_x = 0 on (0, j, 0), u_y = 0 at (0, 0, 0)); uniform pressure q
+    on the top surface, consistent nodal loads q/4 per adjacent unit face.
+    info["passive"]: uint8 per element, 0 active, 1 solid, 2 void."""
     nx, ny, nz = dims
     nn = n_nodes(dims)
     fixed = np.zeros(3 * nn, dtype=np.uint8)
-    fixed[3 * node_index(dims, 0, 0, 0) + np.arange(3)] = 1
-    fixed[3 * node_index(dims, nx, 0, 0) + 1] = 1
-    fixed[3 * node_index(dims, nx, 0, 0) + 2] = 1
-    fixed[3 * node_index(dims, 0, ny, 0) + 2] = 1
-    fixed[3 * node_index(dims, nx, ny, 0) + 2] = 1
+    left = node_index(dims, 0, np.arange(ny + 1), 0)
+    right = node_index(dims, nx, np.arange(ny + 1), 0)
+    fixed[3 * left + 2] = 1
+    fixed[3 * right + 2] = 1
+    fixed[3 * left + 0] = 1
+    fixed[3 * node_index(dims, 0, 0, 0) + 1] = 1
     f = np.zeros(3 * nn)
     wx, wy = _line_weights(nx + 1), _line_weights(ny + 1)
     jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
@@ -175,7 +176,7 @@ def arch_bridge(dims, deck_layers, slot_halfwidth, q=1.0) -> Problem:
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     passive = np.zeros(nx * ny * nz, dtype=np.uint8)
     passive[(k >= nz - deck_layers).ravel()] = 1
-    slot = (np.abs(i + 0.5 - nx / 2) <= slot_halfwidth) & (k < nz - deck_layers)
+    slot = (np.abs(i + 0.5 - nx / 2) <= slot_halfwidth) & (k < nz // 2)
     passive[slot.ravel()] = 2
     return Problem(tuple(dims), fixed, f, name=f"arch_bridge_{nx}x{ny}x{nz}", info=dict(passive=passive))
 
@@ -219,8 +220,9 @@ WORKLOADS = {
         oc=dict(iters=49, rmin=1.5, move=0.2, volfrac=0.12)),
     # bridge stand-ins with non-design regions (Sec. 5, Examples 2 and 4):
     # 140 x 10 x 20 domain at 448 x 32 x 64, deck 1.5 (5 layers) passive
-    # solid, void slot of the 4 elements within 1.5 of mid-span, volume fraction 0.14
-    # of the active region; the gravity variant adds the self-weight load
+    # solid, void slot (the 4 elements within 1.5 of mid-span, lower half),
+    # volume fraction 0.14 of the active region; the gravity variant adds
+    # the self-weight load
     "arch_bridge_448x32x64_passive": dict(
         dims=(448, 32, 64), problem="arch_bridge", levels=5, precision="mixed",
         density=dict(kind="const", value=0.14), rel_tol=1e-8,
@@ -231,6 +233,14 @@ WORKLOADS = {
         density=dict(kind="const", value=0.14), rel_tol=1e-8,
         bridge=dict(deck_layers=5, slot_halfwidth=1.5, q=1.0, weight=0.05),
         oc=dict(iters=30, rmin=1.5, move=0.2, volfrac=0.14)),
+    # the foot-bridge size of the paper's Example 4 (1152 x 64 x 256, 49
+    # iterations, self-weight with non-design regions) on the bridge
+    # stand-in geometry (deck 20 layers, slot at mid-span)
+    "footbridge_1152x64x256_gravity": dict(
+        dims=(1152, 64, 256), problem="arch_bridge", levels=6, precision="mixed",
+        density=dict(kind="const", value=0.125), rel_tol=1e-8,
+        bridge=dict(deck_layers=20, slot_halfwidth=4.5, q=1.0, weight=0.05),
+        oc=dict(iters=49, rmin=1.5, move=0.2, volfrac=0.125)),
     "cantilever_768x384x384_mixed": dict(
         dims=(768, 384, 384), problem="cantilever", levels=7, precision="mixed",
         density=dict(kind="uniform_filtered_clipped", seed=3, lo=0.0, hi=1.0,

@@ -61,7 +61,7 @@ def test_arch_bridge_regions_and_loads():
     pb = synth.arch_bridge(dims, deck_layers=2, slot_halfwidth=1.5, q=2.0)
     pas = pb.info["passive"].reshape(16, 8, 32)
     assert np.all(pas[14:] == 1)
-    assert np.all(pas[:14, :, 15:17] == 2) and np.all(pas[:14, :, 14] == 2) and np.all(pas[:14, :, 17] == 2)
+    assert np.all(pas[:8, :, 14:18] == 2) and np.all(pas[8:14, :, 14:18] == 0)
     assert np.all(pas[:14, :, :14] == 0) and np.all(pas[:14, :, 18:] == 0)
     assert pb.f[2::3].sum() == pytest.approx(-2.0 * 32 * 8)      # resultant of the pressure
-    assert pb.fixed.sum() == 3 + 2 + 1 + 1
+    assert pb.fixed.sum() == 2 * 9 + 9 + 1
