@@ -53,6 +53,8 @@ def parse_args(argv=None):
                          "or stored Galerkin element matrices")
     ap.add_argument("--filter", choices=["density", "sensitivity"], default="density",
                     help="OC loop: density filter (chain rule) or the paper's sensitivity filter")
+    ap.add_argument("--graphs", choices=["on", "off"], default="on",
+                    help="replay PCG iterations from captured CUDA graphs (off: direct launches)")
     ap.add_argument("--oc-iters", type=int, default=0, help="OC loop: iterations (default: the workload's)")
     ap.add_argument("--oc-fp64", choices=["on", "off"], default="on",
                     help="OC loop: also run the all-FP64 loop for the drift comparison")
@@ -362,7 +364,7 @@ def run_ours(args):
     move = w.get("oc", {}).get("move", 0.2)
 
     hom = COARSENING[args.coarsening]
-    g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom))
+    g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom, graphs=int(args.graphs == "on")))
     rho0 = physical_density(g, args.workload, dims, dev)
     volfrac = w.get("oc", {}).get("volfrac", float(rho0.mean()))
     g.set_bc_loads(fixed_d, f_d)
@@ -463,7 +465,8 @@ def run_ours(args):
         "clocks": clocks,
     }
     if args.fp64_ref == "full" and prec != TOPO_FP64:
-        g64 = TopoGrid(dims, Params(levels=levels, precision=TOPO_FP64, homogenize=hom))
+        g64 = TopoGrid(dims, Params(levels=levels, precision=TOPO_FP64, homogenize=hom,
+                                    graphs=int(args.graphs == "on")))
         g64.set_bc_loads(fixed_d, f_d)
         g64.set_density(rho0)
         torch.cuda.synchronize()
@@ -518,7 +521,7 @@ def run_oc_loop(args):
         prec, plabel = TOPO_MIXED, "mixed"
     tol = w.get("rel_tol", 1e-8)
     out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
-           "rel_tol": tol, "rmin": oc["rmin"], "move": oc["move"],
+           "rel_tol": tol, "graphs": args.graphs, "rmin": oc["rmin"], "move": oc["move"],
            "volfrac": oc["volfrac"], "coarsening": args.coarsening, "filter": args.filter}
     bridge = w.get("bridge")
     flt = "sensitivity" if bridge else args.filter     # non-design regions: the paper's scheme
@@ -531,7 +534,8 @@ def run_oc_loop(args):
     out["iterations"] = iters
     runs = {}
     for label, p in (("mixed", prec), ("fp64", TOPO_FP64))[:2 if args.oc_fp64 == "on" else 1]:
-        g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=COARSENING[args.coarsening]))
+        g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=COARSENING[args.coarsening],
+                                  graphs=int(args.graphs == "on")))
         g.set_bc_loads(fixed_d, f_d)
         x = x0.clone()
         dc = torch.empty(ne, dtype=torch.float64, device=dev)

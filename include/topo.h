@@ -77,6 +77,10 @@ typedef struct {
                         /* Galerkin P^T K P, stored as coarse element matrices    */
                         /* (576 FP64 + 576 FP32 values per coarse element, levels */
                         /* 1 .. L-1; not with TOPO_MIXED_BF16)                    */
+    int graphs;         /* 1: each PCG iteration after the first is replayed from */
+                        /* a CUDA graph captured once per handle and precision    */
+                        /* (default); 0: direct launches.  Launch profiling       */
+                        /* (topo_profile_enable) always launches directly         */
 } topo_params;
 
 /* Fills *p with the defaults listed above.  TOPO_BADARG if p is NULL. */
@@ -250,6 +254,7 @@ typedef struct {
     double relres;          /* final FP64 ||f - K u|| / ||f||                   */
     double solve_ms;        /* wall time of the call (host clock, synchronised) */
     int status;             /* topo_status of the solve                          */
+    int graph_replays;      /* CG iterations replayed from a captured CUDA graph */
 } topo_solve_stats;
 
 topo_status topo_get_stats(topo_handle h, topo_solve_stats* out);

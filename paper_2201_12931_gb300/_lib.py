@@ -22,12 +22,12 @@ class TopoParams(C.Structure):
     _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double), ("penal", C.c_double),
                 ("levels", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("inner_max_it", C.c_int),
-                ("max_refine", C.c_int), ("homogenize", C.c_int)]
+                ("max_refine", C.c_int), ("homogenize", C.c_int), ("graphs", C.c_int)]
 
 
 class TopoSolveStats(C.Structure):
     _fields_ = [("outer_steps", C.c_int), ("inner_iters", C.c_int), ("relres", C.c_double),
-                ("solve_ms", C.c_double), ("status", C.c_int)]
+                ("solve_ms", C.c_double), ("status", C.c_int), ("graph_replays", C.c_int)]
 
 
 H = C.c_void_p

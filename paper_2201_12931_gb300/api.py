@@ -36,6 +36,7 @@ class Params:
     inner_max_it: int = 500
     max_refine: int = 12
     homogenize: int = 0
+    graphs: int = 1
 
     def to_c(self) -> L.TopoParams:
         p = L.TopoParams()
@@ -51,6 +52,7 @@ class SolveResult:
     relres: float
     outer_steps: int
     solve_ms: float
+    graph_replays: int = 0
 
 
 def _ptr(t: torch.Tensor, dtype, numel=None, name="tensor"):
@@ -122,7 +124,7 @@ class TopoGrid:
         self._check(st, allow=(L.TOPO_MAXITER,))
         self.generation += 1
         s = self.stats()
-        return out, SolveResult(st, it.value, rr.value, s.outer_steps, s.solve_ms)
+        return out, SolveResult(st, it.value, rr.value, s.outer_steps, s.solve_ms, s.graph_replays)
 
     def compliance_and_sensitivity(self, dc: torch.Tensor | None = None):
         Cv = C.c_double(0.0)

@@ -173,6 +173,11 @@ void free_all(topo_grid* h) {
     delete h->mk32;
     h->mk64 = nullptr;
     h->mk32 = nullptr;
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+    if (h->graph64.exec) cudaGraphExecDestroy(h->graph64.exec);
+    if (h->graph32.exec) cudaGraphExecDestroy(h->graph32.exec);
+    h->graph64.exec = h->graph32.exec = nullptr;
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->prof_ev.clear();
 }
@@ -316,6 +321,7 @@ topo_status topo_default_params(topo_params* p) {
     p->inner_max_it = 500;
     p->max_refine = 12;
     p->homogenize = 0;
+    p->graphs = 1;
     return TOPO_OK;
 }
 
@@ -541,6 +547,7 @@ topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it, double* 
     int iters = 0;
     double relres = 0.0;
     int st = TOPO_OK;
+    h->stats.graph_replays = 0;
     const double ff = h->host_sc[6];
     if (ff == 0.0) {
         CK(h, cudaMemsetAsync(h->x, 0, sizeof(double) * 3 * h->lev[0].g.nn, h->stream));

@@ -79,6 +79,12 @@ struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
     int* info = nullptr;      // device: first non-positive pivot + 1 (0 = ok)
 };
 
+struct PcgGraph {             // one captured PCG iteration (precond, beta, p, K p, alpha, x/r update)
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;   // kernel launches per replay
+    bool failed = false;      // capture not possible: direct launches
+};
+
 struct Scalars {              // device-resident CG scalars
     double rz, rz_new, pq, rr, alpha, beta, ff, aux;
     double rz_old;            // z.r of the previous iteration (flexible beta)
@@ -128,6 +134,8 @@ struct topo_grid {
     double* host_sc = nullptr;      // pinned host mirror
     bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false, bf16_ready = false;
     long long launches = 0;
+    topo::PcgGraph graph64, graph32;   // captured PCG iterations per precision
+    cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
     topo_solve_stats stats{};
     std::string err;
     topo::Ctx ctx() { return topo::Ctx{stream, &launches}; }

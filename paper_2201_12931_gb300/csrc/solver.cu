@@ -29,6 +29,7 @@ struct P<double> {
     static const double* WT(topo_grid* h) { return h->cs.WT64; }
     static double* y(topo_grid* h) { return h->cs.y64; }
     static const double* Ke(Level& l) { return l.Ke64; }
+    static PcgGraph& graph(topo_grid* h) { return h->graph64; }
 };
 template <>
 struct P<float> {
@@ -40,6 +41,7 @@ struct P<float> {
     static const float* WT(topo_grid* h) { return h->cs.WT32; }
     static float* y(topo_grid* h) { return h->cs.y32; }
     static const float* Ke(Level& l) { return l.Ke32; }
+    static PcgGraph& graph(topo_grid* h) { return h->graph32; }
 };
 
 template <typename T>
@@ -220,6 +222,42 @@ int vcycle_bf16(topo_grid* h, int l, const float* f, float* out, double* dot) {
     return dot ? np : 0;
 }
 
+// Captures the launches of body() on the handle's stream into gr (the
+// launch counter is charged per replay, not for the capture); on any
+// failure the handle falls back to direct launches.
+// The capture runs on a private non-blocking stream (the handle's stream
+// may be the legacy default stream, which cannot be captured); the graph is
+// then launched on the handle's stream.
+template <typename F>
+static void capture_graph(topo_grid* h, PcgGraph& gr, F&& body) {
+    cudaGraph_t graph = nullptr;
+    const long long l0 = h->launches;
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->cap_stream = nullptr;
+        gr.failed = true;
+        return;
+    }
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        gr.failed = true;
+        return;
+    }
+    cudaStream_t own = h->stream;
+    h->stream = h->cap_stream;   // every launch of body() goes to the capture
+    body();
+    h->stream = own;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    gr.launches = h->launches - l0;
+    h->launches = l0;
+    if (e != cudaSuccess || !graph || cudaGraphInstantiate(&gr.exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        gr.exec = nullptr;
+        gr.failed = true;
+    }
+    if (graph) cudaGraphDestroy(graph);
+}
+
 // copies the scalars to the pinned mirror and waits for them
 static void fetch_scalars(topo_grid* h) {
     cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
@@ -238,7 +276,8 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
     VBuf<T>& vb = P<T>::vb(l0);
     double rr = rr0;
     *status = TOPO_OK;
-    if (rr <= target_rr) {
+    if (rr <= target_rr || max_it <= 0) {
+        if (rr > target_rr) *status = TOPO_MAXITER;
         *rr_out = rr;
         return 0;
     }
@@ -257,27 +296,51 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
     int np = precond();
     cg_beta(c, h->partials, np, h->sc);   // sets rz (beta unused on the first step)
     cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
-    int it = 0;
-    while (it < max_it) {
-        np = op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
-        cg_alpha(c, h->partials, np, h->sc);
-        cg_update_xr<T>(c, n, h->sc, p, q, x, r, h->partials);
-        reduce_to(c, h->partials, kRedBlocks, &h->sc->rr);
-        ++it;
+    // K p, alpha, x += alpha p, r -= alpha q, r.r (on the stream current in h)
+    auto step_a = [&]() {
+        const Ctx cc = h->ctx();
+        const int npa = op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
+        cg_alpha(cc, h->partials, npa, h->sc);
+        cg_update_xr<T>(cc, n, h->sc, p, q, x, r, h->partials);
+        reduce_to(cc, h->partials, kRedBlocks, &h->sc->rr);
+    };
+    // z = M^-1 r, beta, p = z + beta p, then the next step_a
+    auto step_ba = [&]() {
+        const Ctx cc = h->ctx();
+        const int npb = precond();
+        cg_beta(cc, h->partials, npb, h->sc);
+        if (flexible) {   // BF16 rounding makes M^-1 vary slightly between applications
+            dot_partials<T, T>(cc, n, z, q, h->partials);
+            cg_beta_flexible(cc, h->partials, kRedBlocks, h->sc);
+        }
+        cg_update_p<T>(cc, n, h->sc, z, p);
+        step_a();
+    };
+    // Every iteration after the first is the same sequence of launches on the
+    // same buffers (all scalars live on the device), so it is captured once
+    // into a CUDA graph and replayed; the host only reads r.r between
+    // replays.  Not while launches are being timed one by one.
+    PcgGraph& gr = P<T>::graph(h);
+    const bool use_graph = h->prm.graphs != 0 && !h->prof_on && !gr.failed;
+    step_a();
+    int it = 1;
+    for (;;) {
         fetch_scalars(h);
         rr = h->host_sc[3];
         if (h->host_sc[7] != 0.0 || !std::isfinite(rr)) {
             *status = TOPO_BREAKDOWN;
             break;
         }
-        if (rr <= target_rr) break;
-        np = precond();
-        cg_beta(c, h->partials, np, h->sc);
-        if (flexible) {   // BF16 rounding makes M^-1 vary slightly between applications
-            dot_partials<T, T>(c, n, z, q, h->partials);
-            cg_beta_flexible(c, h->partials, kRedBlocks, h->sc);
+        if (rr <= target_rr || it >= max_it) break;
+        if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, step_ba);
+        if (use_graph && gr.exec) {
+            cudaGraphLaunch(gr.exec, h->stream);
+            h->launches += gr.launches;
+            ++h->stats.graph_replays;
+        } else {
+            step_ba();
         }
-        cg_update_p<T>(c, n, h->sc, z, p);
+        ++it;
     }
     if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;
     *rr_out = rr;

@@ -321,23 +321,40 @@ void launch_mode(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* 
 }
 
 // Dense assembly of the coarsest operator with identity Dirichlet rows.
-// element matrices E_e K0, or the stored Ke[e] of a Galerkin level
+// Dense coarsest operator, deterministic: one thread per (row DOF, neighbour
+// node, column component) gathers, in a fixed order, the <= 8 elements that
+// contain both nodes -- element matrices E_e K0, or the stored Ke[e] of a
+// Galerkin level.  Rows and columns of fixed DOFs stay zero here.
 __global__ void k_assemble(const double* __restrict__ K0, const double* __restrict__ E,
                            const double* __restrict__ Ke, const uint8_t* __restrict__ mask, double* __restrict__ A,
                            int nx, int ny, int nz, int npad) {
-    const int e = blockIdx.x;
-    const int i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
-    const int NX = nx + 1, NY = ny + 1;
-    const double Ee = Ke ? 0.0 : E[e];
-    for (int t = threadIdx.x; t < 576; t += blockDim.x) {
-        const int r = t / 24, s = t % 24;
-        const int ar = r / 3, cr = r % 3, as = s / 3, cs = s % 3;
-        const int nr = (i + (ar & 1)) + NX * ((j + ((ar >> 1) & 1)) + NY * (k + (ar >> 2)));
-        const int ns = (i + (as & 1)) + NX * ((j + ((as >> 1) & 1)) + NY * (k + (as >> 2)));
-        if (((mask[nr] >> cr) & 1u) || ((mask[ns] >> cs) & 1u)) continue;
-        atomicAdd(&A[(long long)(3 * nr + cr) * npad + (3 * ns + cs)],
-                  Ke ? Ke[(long long)e * 576 + t] : Ee * K0[r * 24 + s]);
-    }
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const long long total = 3LL * NX * NY * NZ * 81;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int d = (int)(t % 3);
+    const int o = (int)((t / 3) % 27);
+    const long long rdof = t / 81;
+    const int c = (int)(rdof % 3);
+    const long long nr = rdof / 3;
+    const int i = (int)(nr % NX), j = (int)((nr / NX) % NY), k = (int)(nr / ((long long)NX * NY));
+    const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+    const int i2 = i + dx, j2 = j + dy, k2 = k + dz;
+    if (i2 < 0 || i2 >= NX || j2 < 0 || j2 >= NY || k2 < 0 || k2 >= NZ) return;
+    const long long nc = i2 + (long long)NX * (j2 + (long long)NY * k2);
+    if (((mask[nr] >> c) & 1u) || ((mask[nc] >> d) & 1u)) return;
+    double v = 0.0;
+    for (int ez = (k > k2 ? k : k2) - 1; ez <= (k < k2 ? k : k2); ++ez)
+        for (int ey = (j > j2 ? j : j2) - 1; ey <= (j < j2 ? j : j2); ++ey)
+            for (int ex = (i > i2 ? i : i2) - 1; ex <= (i < i2 ? i : i2); ++ex) {
+                if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || ez < 0 || ez >= nz) continue;
+                const long long e = ex + (long long)nx * (ey + (long long)ny * ez);
+                const int a = (i - ex) + 2 * (j - ey) + 4 * (k - ez);
+                const int b = (i2 - ex) + 2 * (j2 - ey) + 4 * (k2 - ez);
+                const int r = 3 * a + c, s = 3 * b + d;
+                v += Ke ? Ke[e * 576 + r * 24 + s] : E[e] * K0[r * 24 + s];
+            }
+    A[(3 * nr + c) * (long long)npad + 3 * nc + d] = v;
 }
 
 __global__ void k_assemble_diag(const uint8_t* __restrict__ mask, double* __restrict__ A, int n, int npad) {
@@ -473,7 +490,8 @@ int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>&
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const double* Ke,
                      const uint8_t* mask, double* A, int npad) {
     cudaMemsetAsync(A, 0, sizeof(double) * (size_t)npad * npad, c.s);
-    k_assemble<<<(unsigned)g.ne, 128, 0, c.s>>>(K0, E, Ke, mask, A, g.nx, g.ny, g.nz, npad);
+    const long long total = 3 * g.nn * 81;
+    k_assemble<<<(unsigned)((total + 255) / 256), 256, 0, c.s>>>(K0, E, Ke, mask, A, g.nx, g.ny, g.nz, npad);
     TOPO_LAUNCH_CHECK(c);
     k_assemble_diag<<<(npad + 255) / 256, 256, 0, c.s>>>(mask, A, (int)(3 * g.nn), npad);
     TOPO_LAUNCH_CHECK(c);

@@ -133,3 +133,27 @@ def test_maxiter_reported():
     g.set_bc_loads(t(pb.fixed), t(pb.f))
     _, res = g.solve(1e-14, 2)
     assert res.status == TOPO_MAXITER and res.iters == 2
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_graph_replay_is_bitwise_identical(precision):
+    """PCG iterations replayed from the captured CUDA graph launch the same
+    kernels in the same order as direct launches: identical results."""
+    from paper_2201_12931_gb300 import Params, TopoGrid
+    import torch
+    dims, levels = (48, 24, 24), 3
+    rho = oflt.density_filter(synth.uniform_field(dims, 1, 1e-3, 1.0), dims, 1.5)
+    pb = synth.cantilever(dims)
+    out = []
+    for graphs in (1, 0):
+        g = TopoGrid(dims, Params(levels=levels, precision=precision, graphs=graphs))
+        g.set_density(t(rho))
+        g.set_bc_loads(t(pb.fixed), t(pb.f))
+        u = torch.empty(3 * g.nn, dtype=torch.float64, device=cuda_device())
+        _, res = g.solve(1e-10, 2000, out=u)
+        assert res.status == 0
+        out.append((n(u), res))
+    (u1, r1), (u0, r0) = out
+    assert r1.graph_replays > 0 and r0.graph_replays == 0
+    assert r1.iters == r0.iters
+    assert np.array_equal(u1, u0)
