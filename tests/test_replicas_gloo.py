@@ -41,3 +41,27 @@ def test_max_over_ranks_without_group():
     import bench
     assert not dist.is_initialized()
     assert bench.max_over_ranks([3, 4.5]) == [3.0, 4.5]
+
+
+def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
+    """Under torchrun the reference arm (the oracle timed on the host) runs on
+    rank 0 only; the other ranks return without work or output.  The oracle
+    timing itself is replaced by a stub here; its JSON line keeps the
+    contract's keys."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    stub = {"value": 1.5, "unit": "s", "cores": 1, "kind": "oracle", "sample": "stub"}
+    monkeypatch.setattr(bench, "cpu_baseline", lambda args, steps=1, warmup=0: dict(stub))
+    args = bench.parse_args(["--impl", "reference", "--steps", "2", "--warmup", "3"])
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] == 1.5
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"] == {"value": 1.5, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
