@@ -90,6 +90,33 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.topo_destroy_grid(None) == 1
     assert lib.topo_set_density(None, None) == 1
     assert lib.topo_solve_state(None, 1e-8, 10, None, None, None) == 1
+    assert lib.topo_filter(None, 1.5, None, None, 0) == 1
+    assert lib.topo_oc_update(None, 1.5, 0.2, 0.3, None, None, None) == 1
+    assert lib.topo_sensitivity_filter(None, 1.5, 1e-3, None, None, None) == 1
+    assert lib.topo_oc_update_unfiltered(None, 0.2, 0.3, None, None, None, None) == 1
+    assert lib.topo_gravity_load(None, 0.1, None, None, None) == 1
+    assert lib.topo_gravity_sensitivity(None, 0.1, None) == 1
+    assert lib.topo_compliance_and_sensitivity(None, None, None) == 1
+    assert lib.topo_vcycle(None, 0, None, None) == 1
+
+
+def test_params_struct_matches_header(lib):
+    """Every field of topo_params in the header is in the ctypes mirror, in order."""
+    import re
+    from paper_2201_12931_gb300._lib import TopoParams, TopoSolveStats
+    hdr = open(os.path.join(ROOT, "include", "topo.h")).read()
+
+    def fields(struct):
+        body = re.search(r"typedef struct \{([^{}]*)\} " + struct + ";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if decl:
+                names += [v.strip() for v in decl.split(None, 1)[1].split(",")]
+        return names
+    assert fields("topo_params") == [f[0] for f in TopoParams._fields_]
+    assert fields("topo_solve_stats") == [f[0] for f in TopoSolveStats._fields_]
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
