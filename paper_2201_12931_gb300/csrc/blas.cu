@@ -7,6 +7,8 @@
 // pass, so results are bitwise reproducible run to run.
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace topo {
@@ -106,7 +108,36 @@ __global__ void __launch_bounds__(256) k_update_xr(long long n, const Scalars* _
     __shared__ double sh[32];
     const T a = (T)sc->alpha;
     double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    long long i0 = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        // 128-bit accesses; r.r (used only for the stopping test) as FP32
+        // sums of 4 squares added in FP64: one FP64 add per 4 entries
+        // instead of a conversion and an FP64 FMA per entry
+        const long long n4 = n / 4;
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        const float4* q4 = reinterpret_cast<const float4*>(q);
+        float4* x4 = reinterpret_cast<float4*>(x);
+        float4* r4 = reinterpret_cast<float4*>(r);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            const float4 pv = p4[i], qv = q4[i];
+            float4 xv = x4[i], rv = r4[i];
+            xv.x += a * pv.x;
+            xv.y += a * pv.y;
+            xv.z += a * pv.z;
+            xv.w += a * pv.w;
+            rv.x -= a * qv.x;
+            rv.y -= a * qv.y;
+            rv.z -= a * qv.z;
+            rv.w -= a * qv.w;
+            x4[i] = xv;
+            r4[i] = rv;
+            s += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        }
+        i0 = 4 * n4;
+    }
+    for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
         x[i] += a * p[i];
         const T ri = r[i] - a * q[i];
         r[i] = ri;
