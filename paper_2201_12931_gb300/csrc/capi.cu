@@ -378,12 +378,17 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     }
     h->lev.resize(h->L);
     h->npartials = kRedBlocks;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        nsm = 152;
+    }
     for (int l = 0; l < h->L; ++l) {
         Level& lv = h->lev[l];
         lv.g = make_geom(nx >> l, ny >> l, nz >> l);
         lv.scale = (double)(1 << l);
-        lv.op32 = op_launch32(lv.g);
-        lv.op64 = op_launch64(lv.g);
+        lv.op32 = op_launch32(lv.g, nsm);
+        lv.op64 = op_launch64(lv.g, nsm);
         h->npartials = std::max(h->npartials, std::max(lv.op32.ctas(), lv.op64.ctas()));
     }
     topo_status st;

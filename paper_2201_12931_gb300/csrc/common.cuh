@@ -151,8 +151,9 @@ enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3 };
 // out = op(u, f); with dot != nullptr also writes per-CTA partial sums of
 //   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
 // and returns the number of partials written.
-OpLaunch op_launch32(const Geom& g);
-OpLaunch op_launch64(const Geom& g);
+// nsm: multiprocessors of the device (wave-aware z chunking)
+OpLaunch op_launch32(const Geom& g, int nsm);
+OpLaunch op_launch64(const Geom& g, int nsm);
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
             const T* u, const T* f, T* out, T omega, double* dot_partials);

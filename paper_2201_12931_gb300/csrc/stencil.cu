@@ -433,25 +433,44 @@ __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double*
 
 }  // namespace
 
-OpLaunch op_launch(const Geom& g, int ty, int target_ctas) {
+// Launch geometry: x-y tiles of (kOpTX - 1) x (ty - 1) output node columns
+// and z chunks of at least 16 planes (each chunk recomputes one layer and
+// pays about 4.5 extra exchange steps).  At least target_ctas CTAs; beyond
+// that the number of chunks minimises (waves of resident CTAs) x (steps per
+// CTA), so that a last, nearly empty wave does not cost a whole CTA time.
+OpLaunch op_launch(const Geom& g, int ty, int target_ctas, int resident_ctas) {
     OpLaunch L;
     L.g = g;
     L.gx = (g.nx + 1 + kOpTX - 2) / (kOpTX - 1);
     L.gy = (g.ny + 1 + ty - 2) / (ty - 1);
     const long long xy = (long long)L.gx * L.gy;
     const int NZ = g.nz + 1;
-    // enough CTAs for a few waves, but chunks of at least 16 planes (each
-    // chunk recomputes one layer and two exchange steps)
-    const long long gz_target = (target_ctas + xy - 1) / xy;
-    int cz = (int)((NZ + gz_target - 1) / gz_target);
-    cz = cz < 16 ? (NZ < 16 ? NZ : 16) : cz;
-    L.cz = cz;
-    L.gz = (NZ + cz - 1) / cz;
+    const long long gz_min = (target_ctas + xy - 1) / xy;
+    auto chunk = [&](long long gz) {
+        int cz = (int)((NZ + gz - 1) / gz);
+        return cz < 16 ? (NZ < 16 ? NZ : 16) : cz;
+    };
+    int best_cz = chunk(gz_min);
+    double best_cost = -1.0;
+    for (long long gz = gz_min; gz <= 8 * gz_min; ++gz) {
+        const int cz = chunk(gz);
+        const long long gz_eff = (NZ + cz - 1) / cz;
+        const long long waves = (xy * gz_eff + resident_ctas - 1) / resident_ctas;
+        const double cost = (double)waves * (cz + 4.5);
+        if (best_cost < 0.0 || cost < best_cost) {
+            best_cost = cost;
+            best_cz = cz;
+        }
+        if (cz <= 16) break;   // chunks cannot get shorter
+    }
+    L.cz = best_cz;
+    L.gz = (NZ + best_cz - 1) / best_cz;
     return L;
 }
 
-OpLaunch op_launch32(const Geom& g) { return op_launch(g, op_ty<float>(), 1216); }
-OpLaunch op_launch64(const Geom& g) { return op_launch(g, op_ty<double>(), 608); }
+// resident CTAs per SM: 2 for the FP32 kernel (launch bounds 256 x 2), 1 for FP64
+OpLaunch op_launch32(const Geom& g, int nsm) { return op_launch(g, op_ty<float>(), 1216, 2 * nsm); }
+OpLaunch op_launch64(const Geom& g, int nsm) { return op_launch(g, op_ty<double>(), 608, nsm); }
 
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
