@@ -142,3 +142,79 @@ def test_dropped_dirichlet_column_is_caught():
     bad[np.where(fixed)[0], :] = 0.0                          # rows only, columns kept
     bad = bad.tocsr() + sp.diags(fixed.astype(float))
     assert np.abs((bad - bad.T).toarray()).max() > 1e-3
+
+
+# ---- planted mistakes in the added oracle functions -------------------------
+
+def test_sensitivity_filter_without_gamma_clamp_is_caught():
+    """Dividing by rho_e instead of max(gamma, rho_e): the brute-force pin with
+    densities below gamma fails."""
+    dims = (5, 4, 3)
+    rho = synth.uniform_field(dims, 31, 0.0, 1.0)
+    rho[::7] = 1e-4
+    dc = -synth.uniform_field(dims, 32, 0.1, 5.0)
+    ref = flt.density_filter_bruteforce(rho * dc, dims, 1.5) / np.maximum(1e-3, rho)
+    bad = flt.density_filter(rho * dc, dims, 1.5) / rho
+    assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_gravity_term_with_wrong_factor_is_caught():
+    """u_e^T g_e instead of 2 u_e^T g_e: central differences disagree."""
+    dims = (4, 2, 2)
+    pb = synth.cantilever(dims)
+    K0 = element.element_stiffness(0.3)
+    rho = synth.uniform_field(dims, 7, 0.3, 1.0)
+    w = 0.7
+
+    def solve_c(r):
+        f = sensitivity.gravity_load(dims, r, w, pb.f)
+        K, fb = assemble.constrained_system(dims, assemble.simp_modulus(r), K0, pb.fixed, f)
+        u = np.linalg.solve(K.toarray(), fb)
+        return float(fb @ u), u
+
+    _, u = solve_c(rho)
+    se = sensitivity.element_energy(u, dims, K0)
+    bad = sensitivity.sensitivity(rho, se) + 0.5 * sensitivity.gravity_sensitivity_term(dims, u, w)
+    e, h = 3, 1e-6
+    rp, rm = rho.copy(), rho.copy()
+    rp[e] += h
+    rm[e] -= h
+    fd = (solve_c(rp)[0] - solve_c(rm)[0]) / (2 * h)
+    assert abs(bad[e] - fd) > 1e-4 * abs(fd)
+
+
+def test_modulus_rule_without_element_scale_is_caught():
+    """Averaging the moduli but dropping the factor 2 per level: the coarse
+    energy of a linear field no longer matches the fine one."""
+    dims = (8, 8, 4)
+    rho = synth.uniform_field(dims, 21, 0.0, 1.0)
+    K0 = element.element_stiffness(0.3)
+    E = assemble.simp_modulus(rho)
+    Kf = assemble.assemble(dims, E, K0)
+    Ec = multigrid.homogenize_density(E, dims)
+    Kc_bad = assemble.assemble(multigrid.coarse_dims(dims), Ec, K0)          # missing 2 K0
+    A = np.array([[0.3, -0.2, 0.1], [0.05, 0.4, -0.3], [0.2, 0.1, 0.25]])
+
+    def lin(d, h):
+        nx, ny, nz = d
+        k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        X = h * np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(float)
+        return (X @ A.T).ravel()
+    uf, uc = lin(dims, 1.0), lin(multigrid.coarse_dims(dims), 2.0)
+    assert abs(uc @ (Kc_bad @ uc) - uf @ (Kf @ uf)) > 0.3 * abs(uf @ (Kf @ uf))
+
+
+def test_passive_volume_over_all_elements_is_caught():
+    """Bisecting on the volume of all elements instead of the active ones:
+    the active volume fraction misses the target."""
+    from oracle import oc
+    x = np.full(128, 0.3)
+    passive = np.zeros(128, dtype=np.uint8)
+    passive[:16] = 1
+    x[:16] = 1.0
+    dc = -synth.uniform_field((8, 4, 4), 3, 0.1, 10.0)
+    bad = oc.oc_update_unfiltered(x, dc, 0.3, 0.2)[0]        # passive ignored
+    bad[:16] = 1.0
+    good = oc.oc_update_unfiltered(x, dc, 0.3, 0.2, passive=passive)[0]
+    assert abs(good[16:].mean() - 0.3) < 1e-6
+    assert abs(bad[16:].mean() - 0.3) > 1e-2
