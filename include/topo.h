@@ -9,8 +9,13 @@
  * (Eq. K_mod read with K_min = (Emin/E0) K0).  The state equation is solved
  * by CG (Algorithm 1) preconditioned with a Jacobi-smoothed geometric
  * multigrid V-cycle (Algorithm 3) whose coarse operators are formed on the
- * fly from homogenized densities (Sec. 4.2.2, Sec. 6); K.u is applied
- * element by element from one reference matrix K0 (Sec. 4.2.1).
+ * fly from homogenized densities (Sec. 4.2.2, Sec. 6; optionally from
+ * averaged moduli, or stored Galerkin element matrices, see
+ * topo_params.homogenize); K.u is applied element by element from one
+ * reference matrix K0 (Sec. 4.2.1).  Around the solve: compliance and
+ * sensitivity, the density filter and its transpose, the OC update, the
+ * paper's sensitivity filter with the OC step on the design's own volume,
+ * passive (non-design) elements, and the design-dependent self-weight load.
  *
  * Conventions shared by every call
  *   - element id e = i + nx*(j + ny*k); node id n = i + (nx+1)*(j + (ny+1)*k);
