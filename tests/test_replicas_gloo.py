@@ -65,3 +65,30 @@ def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"] == {"value": 1.5, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["higher_is_better"] is False and line["steps"] == 2 and line["warmup"] == 3
+
+
+def test_roofline_entries():
+    """The bench line's roofline objects: HBM-bound FP32 kernels against the
+    measured copy bandwidth, the FP64 residual against the derived FP64 peak."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ne = 1000
+    r32 = {"mode": 0, "prec": 1, "kernel": "K.u (fp32) fine level", "launches": 3, "avg_launch_ms": 0.5,
+           "algorithmic_bytes_per_launch": 2e9, "achieved_gbs": 4000.0, "frac": 0.6}
+    e = bench.roofline_entry(r32, 6700.0, "measured", ne)
+    assert e["bound"] == "hbm" and e["unit"] == "GB/s" and e["peak"] == 6700.0 and e["frac"] == 0.6
+    r64 = {"mode": 2, "prec": 0, "kernel": "residual (fp64) fine level", "launches": 2, "avg_launch_ms": 1.0,
+           "algorithmic_bytes_per_launch": 1e9, "achieved_gbs": 1000.0, "frac": 0.15}
+    e = bench.roofline_entry(r64, 6700.0, "measured", ne)
+    tflops = bench.MODAL_FLOPS_PER_ELEMENT * ne / 1e-3 / 1e12
+    assert e["bound"] == "alu" and e["unit"] == "TFLOP/s" and e["traffic"] is None
+    assert abs(e["achieved"] - round(tflops, 4)) < 1e-9
+    assert abs(e["peak"] - 152 * 4 * 2.07e9 / 1e12) < 1e-3
+    # the dominant kernel is the one with the largest total time
+    rows = [dict(r32, total_ms=1.5), dict(r64, total_ms=2.0)]
+    assert bench.roofline(rows, 6700.0, "measured", ne)["bound"] == "alu"
+    assert bench.ku_roofline(rows, 6700.0, "measured", ne)["bound"] == "hbm"
+    # BF16-iterate kernels count 2-byte iterates
+    nn = 100
+    assert bench.op_bytes(1, 2, nn, ne) == 3 * nn * (2 + 4 + 2) + 4 * ne
+    assert bench.op_bytes(1, 1, nn, ne) == 3 * 3 * nn * 4 + 4 * ne

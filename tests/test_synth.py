@@ -65,3 +65,15 @@ def test_arch_bridge_regions_and_loads():
     assert np.all(pas[:14, :, :14] == 0) and np.all(pas[:14, :, 18:] == 0)
     assert pb.f[2::3].sum() == pytest.approx(-2.0 * 32 * 8)      # resultant of the pressure
     assert pb.fixed.sum() == 2 * 9 + 9 + 1
+
+
+@pytest.mark.parametrize("name", sorted(synth.WORKLOADS))
+def test_workload_hierarchies_are_valid(name):
+    """Every named workload's grid divides by 2^(levels-1) and its coarsest
+    grid fits the dense direct solve (at most 12000 DOFs)."""
+    w = synth.WORKLOADS[name]
+    nx, ny, nz = w["dims"]
+    f = 2 ** (w["levels"] - 1)
+    assert nx % f == 0 and ny % f == 0 and nz % f == 0
+    ndof = 3 * (nx // f + 1) * (ny // f + 1) * (nz // f + 1)
+    assert ndof <= 12000, ndof
