@@ -92,3 +92,16 @@ def test_roofline_entries():
     nn = 100
     assert bench.op_bytes(1, 2, nn, ne) == 3 * nn * (2 + 4 + 2) + 4 * ne
     assert bench.op_bytes(1, 1, nn, ne) == 3 * 3 * nn * 4 + 4 * ne
+
+
+def test_bench_defaults_follow_the_contract():
+    """Defaults: one GPU, at least 3 warm-up steps, a few timed steps, the
+    113M-element workload, the oracle as the reference arm."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.parse_args([])
+    assert a.gpus == 1 and a.warmup >= 3 and 1 <= a.steps <= 10
+    assert a.impl == "ours" and a.workload == "cantilever_768x384x384_mixed"
+    assert a.cpu_baseline == "on" and a.fp64_ref == "full" and a.graphs == "on"
+    r = bench.parse_args(["--impl", "reference", "--gpus", "2", "--steps", "4", "--warmup", "3"])
+    assert r.impl == "reference" and r.gpus == 2 and r.steps == 4
