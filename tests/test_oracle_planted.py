@@ -218,3 +218,39 @@ def test_passive_volume_over_all_elements_is_caught():
     good = oc.oc_update_unfiltered(x, dc, 0.3, 0.2, passive=passive)[0]
     assert abs(good[16:].mean() - 0.3) < 1e-6
     assert abs(bad[16:].mean() - 0.3) > 1e-2
+
+
+def _oc_with_law(law, use_dv=True):
+    """Mutated copy of oracle.oc.oc_update whose unclamped candidate is
+    law(x, B) instead of x B^(1/2); use_dv=False drops the filter transpose
+    of the volume derivative (dv~ = 1)."""
+    def update(x, dc, dims, r, volfrac, move):
+        dct = flt.density_filter_T(dc, dims, r)
+        dvt = flt.density_filter_T(np.ones_like(x), dims, r) if use_dv else np.ones_like(x)
+        num = np.maximum(-dct, 1e-30)
+        l1, l2 = 0.0, 1e9
+        xnew = x.copy()
+        while (l2 - l1) / (l1 + l2) > 1e-9:
+            lmid = 0.5 * (l1 + l2)
+            cand = law(x, num / (lmid * dvt))
+            xnew = np.maximum(0.0, np.maximum(x - move, np.minimum(1.0, np.minimum(x + move, cand))))
+            if flt.density_filter(xnew, dims, r).mean() > volfrac:
+                l1 = lmid
+            else:
+                l2 = lmid
+        return xnew, None
+    return update
+
+
+def test_oc_law_mistakes_are_caught():
+    """eta = 1, the paper's q = 2 on the unclamped value, and a volume
+    derivative without the filter transpose each leave the minimiser of the
+    reciprocal-variable subproblem (the pin in test_oracle_oc_law.py);
+    the law as read (eta = 1/2, q = 1) passes through the same copy."""
+    from test_oracle_oc_law import _filtered_case, oc_law_error
+    case = _filtered_case()
+    assert oc_law_error(_oc_with_law(lambda x, B: x * np.sqrt(B)), *case)[0] < 1e-6
+    for bad in (_oc_with_law(lambda x, B: x * B),
+                _oc_with_law(lambda x, B: (x * np.sqrt(B)) ** 2),
+                _oc_with_law(lambda x, B: x * np.sqrt(B), use_dv=False)):
+        assert oc_law_error(bad, *case)[0] > 1e-3
