@@ -60,7 +60,10 @@ def parse_args(argv=None):
                     help="OC loop: also run the all-FP64 loop for the drift comparison")
     ap.add_argument("--oc-loop", action="store_true",
                     help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
+    ap.add_argument("--oracle-table", choices=["on", "off"], default="on",
+                    help="time the oracle and the GPU path on the small configurations (C1-C3) in the same run")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
@@ -150,8 +153,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the oracle, single-threaded, on a bounded sample
+# CPU baseline: the oracle on the host's cores, on a bounded sample
 # ---------------------------------------------------------------------------
+
+def host_threads():
+    """Cores this process may run on (the oracle's thread budget)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _cpu_seconds():
+    import resource
+    r = resource.getrusage(resource.RUSAGE_SELF)
+    return r.ru_utime + r.ru_stime
+
+
+def oracle_env():
+    n = str(host_threads())
+    return dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n)
 
 def cpu_sample(name, dims, rel_tol):
     """Oracle state solve of the workload recipe at `dims`; returns seconds."""
@@ -171,25 +192,30 @@ def cpu_sample(name, dims, rel_tol):
 
 
 def run_cpu_child(args):
-    _, _, _ = None, None, None
     w, dims, _ = workload(args)
     sample = CPU_SAMPLE_DIMS
     times = []
+    c0, t0 = _cpu_seconds(), time.perf_counter()
     for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            c0, t0 = _cpu_seconds(), time.perf_counter()
         t, info = cpu_sample(args.workload, sample, args.rel_tol)
         if i >= args.warmup:
             times.append(t)
-    print(json.dumps({"times": times, "sample_dims": sample, "iters": info["iters"]}))
+    util = (_cpu_seconds() - c0) / max(time.perf_counter() - t0, 1e-9)
+    print(json.dumps({"times": times, "sample_dims": sample, "iters": info["iters"], "cpu_util": util}))
 
 
-def cpu_baseline(args, steps=1, warmup=0):
-    """Spawns the oracle in a fresh single-threaded process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_baseline(args, steps=3, warmup=1):
+    """Spawns the oracle in a fresh process allowed all host cores; one
+    untimed solve, then `steps` timed ones of the bounded sample, scaled to
+    the workload by element count (multigrid work is linear in it)."""
+    cores = host_threads()
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", "--workload", args.workload,
            "--steps", str(steps), "--warmup", str(warmup), "--rel-tol", str(args.rel_tol)]
     if args.dims:
         cmd += ["--dims", args.dims]
-    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    out = subprocess.run(cmd, capture_output=True, text=True, env=oracle_env(), timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     res = json.loads(out.stdout.strip().splitlines()[-1])
@@ -201,12 +227,133 @@ def cpu_baseline(args, steps=1, warmup=0):
     return {
         "value": t * scale,
         "unit": "s",
-        "cores": 1,
+        "cores": cores,
         "kind": "oracle",
+        "extrapolated": True,
+        "scale_factor": round(scale, 3),
+        "sample_s": round(t, 4),
+        "cpu_utilisation": round(res["cpu_util"], 2),
         "sample": (f"oracle FP64 state solve (assembled CSR K, Galerkin-MG PCG to rel. residual {args.rel_tol:g}, "
-                   f"{res['iters']} it) of the same recipe on a {s[0]}x{s[1]}x{s[2]} grid: "
-                   f"{t:.2f} s, scaled by element count x{scale:.0f} to {dims[0]}x{dims[1]}x{dims[2]}"),
+                   f"{res['iters']} it) of the same recipe on a {s[0]}x{s[1]}x{s[2]} grid, mean of {steps} after "
+                   f"{warmup} untimed, {cores} threads allowed: {t:.2f} s, extrapolated by element count "
+                   f"x{scale:.0f} to {dims[0]}x{dims[1]}x{dims[2]}"),
     }
+
+
+# the small configurations both the oracle and the GPU path run in full
+ORACLE_TABLE = (
+    ("C1", "cantilever_48x24x24_fp64_oc20", "s per OC iteration (density filter, solve to 1e-8, sensitivity, OC)"),
+    ("C2", "cantilever_128x64x64_mixed", "s per state solve to rel. residual 1e-8 from u = 0"),
+    ("C3", "mbb_96x48x48_grad", "s per compliance gradient (filter, solve to 1e-10, sensitivity, filter transpose)"),
+)
+
+
+def run_oracle_child(label):
+    """One configuration of ORACLE_TABLE on the oracle, timed in this process."""
+    import synth
+    from oracle import filter as oflt, state as ostate
+    _, name, _ = next(c for c in ORACLE_TABLE if c[0] == label)
+    w = synth.WORKLOADS[name]
+    dims = tuple(w["dims"])
+    pb = synth.make_problem(name)
+    x = synth.raw_density(name)
+    c0, t0 = _cpu_seconds(), time.perf_counter()
+    if label == "C1":
+        oc = w["oc"]
+        ostate.oc_iteration(dims, x, pb.fixed, pb.f, oc["rmin"], oc["volfrac"], oc["move"], tol=w["rel_tol"])
+        detail = "1 iteration from x = 0.3"
+    elif label == "C2":
+        rho = oflt.density_filter(x, dims, w["density"]["rmin"])
+        c0, t0 = _cpu_seconds(), time.perf_counter()     # the input filter is not part of the solve
+        _, info = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=1e-8, method="mgpcg", return_info=True)
+        detail = f"Galerkin-MG PCG, {info['iters']} it"
+    else:
+        rmin = w["density"]["rmin"]
+        rho = oflt.density_filter(x, dims, rmin)
+        u = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=1e-10, method="mgpcg")
+        _, _, dc = ostate.compliance_and_sensitivity(dims, rho, u, pb.f)
+        oflt.density_filter_T(dc, dims, rmin)
+        detail = "Galerkin-MG PCG"
+    wall = time.perf_counter() - t0
+    print(json.dumps({"s": wall, "cpu_util": (_cpu_seconds() - c0) / max(wall, 1e-9), "detail": detail}))
+
+
+def oracle_time(label):
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", label]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=oracle_env(), timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def gpu_time(label, dev):
+    """The same configuration on the GPU path: CUDA-event time, median of 3
+    after one untimed repetition (C1: mean over the 20-iteration loop)."""
+    import torch
+    import synth
+    from paper_2201_12931_gb300 import Params, TopoGrid, TOPO_FP64, TOPO_MIXED
+    from paper_2201_12931_gb300.autograd import compliance
+    _, name, _ = next(c for c in ORACLE_TABLE if c[0] == label)
+    w = synth.WORKLOADS[name]
+    dims = tuple(w["dims"])
+    pb = synth.make_problem(name)
+    prec = TOPO_FP64 if w["precision"] == "fp64" else TOPO_MIXED
+    g = TopoGrid(dims, Params(levels=w["levels"], precision=prec))
+    g.set_bc_loads(torch.tensor(pb.fixed, device=dev), torch.tensor(pb.f, device=dev))
+    x0 = torch.tensor(synth.raw_density(name), device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    times = []
+    if label == "C1":
+        oc = w["oc"]
+        x = x0.clone()
+        dc = torch.empty(g.ne, dtype=torch.float64, device=dev)
+        for _ in range(oc["iters"]):
+            a, b = ev(), ev()
+            a.record()
+            g.set_density(g.filter(oc["rmin"], x))
+            g.solve(w["rel_tol"], 20000)
+            g.compliance_and_sensitivity(dc)
+            g.oc_update(oc["rmin"], oc["move"], oc["volfrac"], x, dc)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+        t = statistics.mean(times[1:])
+        detail = f"mean of iterations 2-{oc['iters']} of the loop, {w['precision']}"
+    else:
+        rmin = w["density"]["rmin"]
+        for i in range(4):
+            a, b = ev(), ev()
+            if label == "C2":
+                g.set_density(g.filter(rmin, x0))
+                g.reset_solution()
+                a.record()
+                g.solve(1e-8, 20000)
+                b.record()
+            else:
+                xr = x0.clone().requires_grad_(True)
+                g.reset_solution()
+                a.record()
+                compliance(xr, g, rmin, rel_tol=1e-10).backward()
+                b.record()
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(a.elapsed_time(b) / 1e3)
+        t = statistics.median(times)
+        detail = f"median of 3 after one untimed, {w['precision']}"
+    g.close()
+    return t, detail
+
+
+def oracle_table(dev):
+    rows = []
+    for label, name, unit in ORACLE_TABLE:
+        o = oracle_time(label)
+        tg, dg = gpu_time(label, dev)
+        rows.append({"config": label, "workload": name, "unit": unit, "oracle_s": round(o["s"], 4),
+                     "oracle_detail": o["detail"], "oracle_cores": host_threads(),
+                     "oracle_cpu_utilisation": round(o["cpu_util"], 2), "gpu_s": round(tg, 5), "gpu_detail": dg,
+                     "oracle_over_gpu": round(o["s"] / tg, 1)})
+    return rows
 
 
 # ---------------------------------------------------------------------------
@@ -223,16 +370,19 @@ def peaks():
 
 
 OP_NAMES = {0: "K.u", 1: "Jacobi sweep", 2: "residual", 3: "first Jacobi sweep"}
+PREC_NAMES = ("fp64", "fp32", "fp32, bf16 iterates", "double-fp32", "fp32, tensor-core element products")
 
 
 def op_bytes(mode, prec, nn, ne):
     """Algorithmic HBM bytes of one fine-level operator launch: the nodal
     vectors it must read and write (3 DOFs per node) plus one modulus per
     element; s = 8 (FP64 kernel) or 4 (FP32 kernel)."""
+    if prec == 3:   # double-FP32 arithmetic on FP64 u, f, E; residual written as FP32, K.u as FP64
+        return 3 * nn * ({0: 8 + 8, 2: 8 + 8 + 4}[mode]) + ne * 8
     if prec == 2:   # BF16 iterates u (in) and u' (out, FP32 for the last sweep), FP32 f and residual
         su, sf, so = 2, 4, 2
         return 3 * nn * ({0: su + so, 1: su + sf + so, 2: su + sf + 4, 3: sf + so}[mode]) + ne * 4
-    s = 8 if prec == 0 else 4
+    s = 8 if prec == 0 else 4   # prec 1 and 4: FP32 vectors
     nvec = {0: 2, 1: 3, 2: 3, 3: 2}[mode]   # K.u: u, y | Jacobi: u, f, u' | residual: u, f, r | first: f, u'
     return nvec * 3 * nn * s + ne * s
 
@@ -242,13 +392,13 @@ def kernel_table(grid, nn, ne):
     rows = []
     for mode in range(4):
         cnt, ms = grid.profile_read(mode)
-        for prec in (0, 1, 2):
+        for prec in (0, 1, 2, 3, 4):
             if not cnt[prec]:
                 continue
             b = op_bytes(mode, prec, nn, ne)
             avg = ms[prec] / cnt[prec]
             gbs = b / (avg / 1e3) / 1e9
-            rows.append({"kernel": f"{OP_NAMES[mode]} ({('fp64', 'fp32', 'fp32, bf16 iterates')[prec]}) fine level",
+            rows.append({"kernel": f"{OP_NAMES[mode]} ({PREC_NAMES[prec]}) fine level",
                          "mode": mode, "prec": prec, "launches": cnt[prec], "total_ms": round(ms[prec], 3),
                          "avg_launch_ms": round(avg, 4), "algorithmic_bytes_per_launch": b,
                          "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4)})
@@ -284,24 +434,45 @@ def measured_traffic(mode, prec, ne):
     return None
 
 
-# FP64 peak of the GB300 CUDA cores: 152 SMs x 4 FP64 flops per cycle (two
-# FMA lanes) x 2.07 GHz maximum SM clock = 1.259 TFLOP/s (nominal 1.25)
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+_ALU = {}
+
+
+def alu_peaks():
+    """FP64 / FP32 FMA peaks of this GPU in TFLOP/s, measured once per process
+    with the library's own microbenchmark (topo_measure_peak)."""
+    if not _ALU:
+        from paper_2201_12931_gb300.api import measure_peak
+        for kind, name in ((0, "fp64"), (1, "fp32"), (2, "fp32x2")):
+            tf, ms = measure_peak(kind)
+            _ALU[name] = round(tf, 3)
+            _ALU[name + "_ms"] = round(ms, 4)
+    return _ALU
 # algorithmic FP64 flops of one element in the modal operator (FMA = 2):
 # in-plane transform of the new face 24, z butterfly 21, modulus scaling 8,
 # modal block stiffness 33, inverse z butterfly 21, face accumulation 12,
 # inverse in-plane transform 24, corner sums and residual 12
 MODAL_FLOPS_PER_ELEMENT = 24 + 21 + 8 + 33 + 21 + 12 + 24 + 12
+# FP32 flops of one element of the double-FP32 residual: the same operator as
+# 133 pair additions (TwoSum of the high words + two low-word adds = 8 flops)
+# and 34 pair products (one multiply and three FMAs = 7 flops)
+DF_FLOPS_PER_ELEMENT = 133 * 8 + 34 * 7
 
 
 def roofline_entry(r, peak, src, ne):
-    if r["prec"] == 0:   # FP64 operator: bound by the FP64 pipe, not by HBM
-        tflops = MODAL_FLOPS_PER_ELEMENT * ne / (r["avg_launch_ms"] / 1e3) / 1e12
-        return {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": None, "kernel": r["kernel"],
+    if r["prec"] in (0, 3):   # FP64 / double-FP32 operators: bound by the arithmetic pipes, not by HBM
+        alu = alu_peaks()
+        fl = (MODAL_FLOPS_PER_ELEMENT if r["prec"] == 0 else DF_FLOPS_PER_ELEMENT) * ne
+        pk = alu["fp64"] if r["prec"] == 0 else max(alu["fp32"], alu["fp32x2"])
+        tflops = fl / (r["avg_launch_ms"] / 1e3) / 1e12
+        tr = measured_traffic(r["mode"], r["prec"], ne)
+        return {"bound": "alu", "achieved": round(tflops, 4), "peak": pk, "unit": "TFLOP/s",
+                "frac": round(tflops / pk, 4), "traffic": None if tr is None else int(tr), "kernel": r["kernel"],
                 "launches": r["launches"], "avg_launch_ms": r["avg_launch_ms"],
-                "algorithmic_flops_per_launch": MODAL_FLOPS_PER_ELEMENT * ne,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/cycle x 2.07 GHz"}
+                "algorithmic_flops_per_launch": fl,
+                "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"],
+                "achieved_gbs": r["achieved_gbs"],
+                "peak_source": "measured: topo_measure_peak " + ("FP64" if r["prec"] == 0 else "FP32")
+                               + " FMA chains, this GPU, this run"}
     tr = measured_traffic(r["mode"], r["prec"], ne)
     return {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s", "frac": r["frac"],
             "traffic": None if tr is None else int(tr), "kernel": r["kernel"], "launches": r["launches"],
@@ -318,7 +489,7 @@ def roofline(rows, peak, src, ne):
 
 def ku_roofline(rows, peak, src, ne):
     """The FP32 K.u kernel of the metric (HBM-bound form), whatever its share."""
-    r = [v for v in rows if v["mode"] == 0 and v["prec"] == 1]
+    r = [v for v in rows if v["mode"] == 0 and v["prec"] in (1, 4)]
     return roofline_entry(r[0], peak, src, ne) if r else None
 
 
@@ -462,6 +633,7 @@ def run_ours(args):
         "roofline": roof,
         "roofline_ku": roof_ku,
         "operator_kernels": rows,
+        "alu_peaks_tflops": alu_peaks(),
         "clocks": clocks,
     }
     if args.fp64_ref == "full" and prec != TOPO_FP64:
@@ -469,16 +641,31 @@ def run_ours(args):
                                     graphs=int(args.graphs == "on")))
         g64.set_bc_loads(fixed_d, f_d)
         g64.set_density(rho0)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        _, r64 = g64.solve(args.fp64_tol, 20000)
-        t64 = time.perf_counter() - t1
+        # timed like the mixed arm: untimed warm-up solve, then CUDA events
+        # around solves from u = 0 with launch profiling on (direct launches)
+        g64.solve(args.fp64_tol, 20000)
+        g64.profile_enable(True)
+        t64s = []
+        for _ in range(3):
+            g64.reset_solution()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, r64 = g64.solve(args.fp64_tol, 20000)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t64s.append(a.elapsed_time(b) / 1e3)
+        g64.profile_enable(False)
+        t64 = statistics.median(t64s)
         C64_tol, _ = g64.compliance_and_sensitivity()
-        _, r64b = g64.solve(1e-10, 20000)
+        _, r64b = g64.solve(1e-10, 20000)      # warm-started from the solution at fp64_tol
         C_ref, _ = g64.compliance_and_sensitivity()
-        out["fp64_gpu"] = {"solve_s": round(t64, 4), "rel_tol": args.fp64_tol, "iters": r64.iters,
+        out["fp64_gpu"] = {"solve_s": round(t64, 4), "solve_s_all": [round(v, 4) for v in t64s],
+                           "timing": "median of 3 solves from u = 0 after one untimed, CUDA events, "
+                                     "launch profiling on as in the mixed arm",
+                           "rel_tol": args.fp64_tol, "iters": r64.iters,
                            "status": r64.status, "compliance_rel_err": abs(C64_tol - C_ref) / abs(C_ref),
                            "compliance_at_tol": C64_tol, "reference_compliance_1e-10": C_ref,
+                           "reference": "FP64 solve to 1e-10 warm-started from the fp64_tol solution",
                            "reference_status": r64b.status, "reference_iters": r64b.iters}
         out["compliance_rel_err_mixed_vs_fp64_ref"] = abs(C_mixed - C_ref) / abs(C_ref)
         out["mixed_speedup_vs_fp64"] = round(t64 / t_solve, 3)
@@ -488,6 +675,11 @@ def run_ours(args):
             out["cpu_baseline"] = cpu_baseline(args)
         except Exception as e:   # the bench line must still print
             out["cpu_baseline"] = {"error": str(e)[-300:]}
+    if rank == 0 and world == 1 and args.oracle_table == "on":
+        try:
+            out["oracle_configs"] = oracle_table(dev)
+        except Exception as e:
+            out["oracle_configs"] = {"error": str(e)[-300:]}
     g.close()
     if rank == 0:
         print(json.dumps(out))
@@ -604,6 +796,8 @@ def main():
     args = parse_args()
     if args.cpu_child:
         run_cpu_child(args)
+    elif args.oracle_child:
+        run_oracle_child(args.oracle_child)
     elif args.oc_loop:
         run_oc_loop(args)
     elif args.impl == "reference":

@@ -58,8 +58,15 @@ typedef enum {
 typedef enum {
     TOPO_FP64 = 0,       /* all vectors and arithmetic in FP64                */
     TOPO_MIXED = 1,      /* FP32 inner MGPCG inside FP64 iterative refinement */
-    TOPO_MIXED_BF16 = 2  /* as TOPO_MIXED, V-cycle iterates stored in BF16 on */
+    TOPO_MIXED_BF16 = 2, /* as TOPO_MIXED, V-cycle iterates stored in BF16 on */
                          /* all levels above the coarsest (FP32 arithmetic)  */
+    TOPO_DF32 = 3,       /* step-level K.u and residual only (not a handle    */
+                         /* precision): FP64 vectors and moduli, arithmetic  */
+                         /* in double-FP32 pairs on the FP32 pipe -- the     */
+                         /* outer residual of the mixed solves               */
+    TOPO_FP32_TC = 4     /* step-level K.u, Jacobi sweep and residual only:   */
+                         /* the FP32 operator with its element products on   */
+                         /* the tensor cores (topo_params.tensor_cores)      */
 } topo_precision;
 
 /* Solver and material parameters.  Defaults from topo_default_params. */
@@ -86,6 +93,15 @@ typedef struct {
                         /* a CUDA graph captured once per handle and precision    */
                         /* (default); 0: direct launches.  Launch profiling       */
                         /* (topo_profile_enable) always launches directly         */
+    int outer_residual; /* FP64-accurate residual r = f - K x of the refinement   */
+                        /* loop of the mixed modes: 0 = double-FP32 kernel on the */
+                        /* FP32 pipe, written straight into the FP32 right-hand  */
+                        /* side of the inner solve (default); 1 = FP64 kernel     */
+    int tensor_cores;   /* FP32 K.u, Jacobi sweeps and residuals of the inner     */
+                        /* solve: 0 = modal kernel on the CUDA cores (default);   */
+                        /* 1 = element products K0 (u_e - u_e0) on the tcgen05    */
+                        /* tensor cores, TF32 operands split hi + lo (about 22    */
+                        /* bits), FP32 accumulation in tensor memory              */
 } topo_params;
 
 /* Fills *p with the defaults listed above.  TOPO_BADARG if p is NULL. */
@@ -126,7 +142,16 @@ topo_status topo_set_bc_loads(topo_handle h, const uint8_t* fixed_dev, const dou
  * residual is recomputed after each inner FP32 solve (iterative refinement).
  * max_it caps the total number of inner CG iterations.  u_dev_out (device,
  * 3*nodes FP64) may be NULL.  iters_out / relres_out (host) may be NULL.
- * Returns TOPO_MAXITER with the best iterate when not converged. */
+ * The FP64 outer residual of the mixed modes is computed by the double-FP32
+ * kernel or the FP64 kernel (topo_params.outer_residual).
+ * Returns TOPO_MAXITER with the best iterate when not converged, and
+ * TOPO_BREAKDOWN when the problem is singular: a non-positive pivot of the
+ * coarsest-grid factorisation (too few Dirichlet conditions: no iteration
+ * runs and the warm start is returned with its FP64 residual), or
+ * non-positive curvature or a non-finite value in CG (the step is not taken:
+ * the last finite iterate and its FP64 residual are returned).  The message
+ * is in topo_last_error; the handle stays usable (e.g. after
+ * topo_set_bc_loads with a well-posed problem). */
 topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it,
                              double* u_dev_out, int* iters_out, double* relres_out);
 
@@ -165,7 +190,7 @@ topo_status topo_oc_update(topo_handle h, double r, double move, double volfrac,
  * w_ei = max(0, r - |x_i - x_e|) over the neighbourhood cut at the domain
  * boundary, S_e = sum_i w_ei (the weights of topo_filter).  rho_dev, dc_dev,
  * out_dev: device, nx*ny*nz FP64; out must not overlap the inputs.
- * 0 < r <= 6, gamma > 0 (the paper: "a small number"; 1e-3 is typical),
+ * 0 < r <= 6, gamma > 0 (the paper only asks for a small positive value; 1e-3 is typical),
  * else TOPO_BADARG. */
 topo_status topo_sensitivity_filter(topo_handle h, double r, double gamma, const double* rho_dev,
                                     const double* dc_dev, double* out_dev);
@@ -208,9 +233,15 @@ const char* topo_last_error(topo_handle h);
  * Step-level entry points.  Each runs one step of the hot path in isolation
  * so that it can be checked against the oracle; the solver uses the same
  * kernels.  Vectors are device, 3*nodes(level) FP64, node-major; `precision`
- * selects the FP64 kernel (TOPO_FP64) or the FP32 kernel (inputs rounded to
- * FP32, result widened to FP64).  TOPO_BADARG for a level outside
- * [0, levels) or NULL pointers.
+ * selects the FP64 kernel (TOPO_FP64), the FP32 kernel (TOPO_MIXED: inputs
+ * rounded to FP32, result widened to FP64) or, for topo_apply_operator and
+ * topo_residual, the double-FP32 kernel (TOPO_DF32: FP64 inputs split into
+ * pairs of FP32 numbers, error-free sums and products of Knuth and Dekker,
+ * result rounded to FP64; about 2^-44 relative to the element terms instead
+ * of FP64's 2^-52), or, for topo_apply_operator, topo_jacobi_sweep and
+ * topo_residual, the FP32 kernel with tensor-core element products
+ * (TOPO_FP32_TC; TOPO_CUDA if a bounded wait on the tensor cores ran out).  TOPO_BADARG for a level outside [0, levels), a
+ * precision the entry point does not offer, or NULL pointers.
  * ------------------------------------------------------------------------- */
 
 /* Grid of a level: elements per axis (l = 0 is the fine grid). */
@@ -281,8 +312,21 @@ topo_status topo_profile_enable(topo_handle h, int on);
  * 1 = Jacobi sweep, 2 = residual, 3 = first sweep from zero), the number of
  * recorded launches and their summed device time in milliseconds, split by
  * kernel precision: index 0 = FP64, 1 = FP32, 2 = FP32 arithmetic with BF16
- * iterates (V-cycle of TOPO_MIXED_BF16) -- arrays of length 3. */
+ * iterates (V-cycle of TOPO_MIXED_BF16), 3 = double-FP32 (outer residual of
+ * the mixed solves), 4 = FP32 with tensor-core element products -- arrays of
+ * length 5. */
 topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms);
+
+/* Arithmetic peak of the CUDA cores, measured (instrumentation; no
+ * counterpart in the paper): a full-occupancy grid of independent fused
+ * multiply-add chains, timed with CUDA events on `stream` (cudaStream_t,
+ * NULL = legacy default stream), best of three launches after a warm-up.
+ * kind 0 = FP64 FMA, 1 = FP32 FMA, 2 = paired FP32 FMA (f32x2).  Returns
+ * TFLOP/s (2 flops per FMA) in *tflops_out and the launch time in *ms_out.
+ * Allocates and frees one small output buffer (8 blocks per SM x 256
+ * threads x 8 bytes).  TOPO_BADARG for another kind or NULL outputs (message
+ * from topo_last_error(NULL)), TOPO_OOM, TOPO_CUDA. */
+topo_status topo_measure_peak(int kind, void* stream, double* tflops_out, double* ms_out);
 
 /* Density filter for callers that cannot allocate GPU memory (no counterpart
  * in the paper).  Same result as topo_filter on a handle of the same grid,

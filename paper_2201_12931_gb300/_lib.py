@@ -15,14 +15,15 @@ LIB_PATH = os.path.join(HERE, "libtopo_gb300.so")
 TOPO_OK, TOPO_BADARG, TOPO_OOM, TOPO_MAXITER, TOPO_BREAKDOWN, TOPO_CUDA = range(6)
 STATUS_NAMES = {0: "TOPO_OK", 1: "TOPO_BADARG", 2: "TOPO_OOM", 3: "TOPO_MAXITER", 4: "TOPO_BREAKDOWN",
                 5: "TOPO_CUDA"}
-TOPO_FP64, TOPO_MIXED, TOPO_MIXED_BF16 = 0, 1, 2
+TOPO_FP64, TOPO_MIXED, TOPO_MIXED_BF16, TOPO_DF32, TOPO_FP32_TC = 0, 1, 2, 3, 4
 
 
 class TopoParams(C.Structure):
     _fields_ = [("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double), ("penal", C.c_double),
                 ("levels", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("inner_max_it", C.c_int),
-                ("max_refine", C.c_int), ("homogenize", C.c_int), ("graphs", C.c_int)]
+                ("max_refine", C.c_int), ("homogenize", C.c_int), ("graphs", C.c_int),
+                ("outer_residual", C.c_int), ("tensor_cores", C.c_int)]
 
 
 class TopoSolveStats(C.Structure):
@@ -57,6 +58,7 @@ _SIGS = {
     "topo_vcycle": ([H, C.c_int, P, P], C.c_int),
     "topo_get_stats": ([H, C.POINTER(TopoSolveStats)], C.c_int),
     "topo_launch_count": ([H, C.POINTER(C.c_longlong)], C.c_int),
+    "topo_measure_peak": ([C.c_int, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "topo_reset_solution": ([H], C.c_int),
     "topo_profile_enable": ([H, C.c_int], C.c_int),
     "topo_profile_read": ([H, C.c_int, C.POINTER(C.c_longlong), C.POINTER(C.c_double)], C.c_int),

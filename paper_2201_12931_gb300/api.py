@@ -37,6 +37,8 @@ class Params:
     max_refine: int = 12
     homogenize: int = 0
     graphs: int = 1
+    outer_residual: int = 0
+    tensor_cores: int = 0
 
     def to_c(self) -> L.TopoParams:
         p = L.TopoParams()
@@ -115,13 +117,15 @@ class TopoGrid:
                                                _ptr(f, torch.float64, 3 * self.nn, "f")))
         self.generation += 1
 
-    def solve(self, rel_tol=1e-8, max_it=1000, out: torch.Tensor | None = None):
-        """Returns (u or None, SolveResult).  TOPO_MAXITER is reported, not raised."""
+    def solve(self, rel_tol=1e-8, max_it=1000, out: torch.Tensor | None = None, allow_breakdown=False):
+        """Returns (u or None, SolveResult).  TOPO_MAXITER is reported, not
+        raised; TOPO_BREAKDOWN too with allow_breakdown (the best iterate and
+        its residual are returned either way)."""
         it = C.c_int(0)
         rr = C.c_double(0.0)
         up = _ptr(out, torch.float64, 3 * self.nn, "out") if out is not None else None
         st = self.lib.topo_solve_state(self._h, rel_tol, max_it, up, C.byref(it), C.byref(rr))
-        self._check(st, allow=(L.TOPO_MAXITER,))
+        self._check(st, allow=(L.TOPO_MAXITER,) + ((L.TOPO_BREAKDOWN,) if allow_breakdown else ()))
         self.generation += 1
         s = self.stats()
         return out, SolveResult(st, it.value, rr.value, s.outer_steps, s.solve_ms, s.graph_replays)
@@ -248,9 +252,10 @@ class TopoGrid:
 
     def profile_read(self, mode: int):
         """(launches, total_ms) per kernel precision [fp64, fp32, fp32 with BF16
-        iterates] for operator kind `mode`."""
-        n = (C.c_longlong * 3)()
-        ms = (C.c_double * 3)()
+        iterates, double-fp32, fp32 with tensor-core element products] for
+        operator kind `mode`."""
+        n = (C.c_longlong * 5)()
+        ms = (C.c_double * 5)()
         self._check(self.lib.topo_profile_read(self._h, mode, n, ms))
         return list(n), list(ms)
 
@@ -258,3 +263,16 @@ class TopoGrid:
         v = C.c_longlong(0)
         self._check(self.lib.topo_launch_count(self._h, C.byref(v)))
         return v.value
+
+
+def measure_peak(kind: int, stream=None):
+    """Measured arithmetic peak of the CUDA cores (topo_measure_peak):
+    kind 0 = FP64 FMA, 1 = FP32 FMA, 2 = paired FP32 FMA.  Returns
+    (TFLOP/s, launch ms)."""
+    lib = L.load()
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    st = lib.topo_measure_peak(kind, C.c_void_p(s), C.byref(tf), C.byref(ms))
+    if st != L.TOPO_OK:
+        raise TopoError(st, lib.topo_last_error(None).decode())
+    return tf.value, ms.value

@@ -167,12 +167,14 @@ void free_all(topo_grid* h) {
     F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
     F(h->K0d); F(h->K0f);
     F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->G64); F(h->oc_dv); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
-    F(h->lam); F(h->dtmp); F(h->dflag); F(h->partials); F(h->sc);
+    F(h->lam); F(h->dtmp); F(h->dflag); F(h->tc_err); F(h->tcB); F(h->partials); F(h->sc);
     if (h->host_sc) cudaFreeHost(h->host_sc);
     delete h->mk64;
     delete h->mk32;
+    delete h->mkdf;
     h->mk64 = nullptr;
     h->mk32 = nullptr;
+    h->mkdf = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
     if (h->graph64.exec) cudaGraphExecDestroy(h->graph64.exec);
@@ -322,6 +324,8 @@ topo_status topo_default_params(topo_params* p) {
     p->max_refine = 12;
     p->homogenize = 0;
     p->graphs = 1;
+    p->outer_residual = 0;
+    p->tensor_cores = 0;
     return TOPO_OK;
 }
 
@@ -344,6 +348,8 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     if (!(p.inner_tol > 0.0 && p.inner_tol < 1.0) || p.inner_max_it < 1 || p.max_refine < 1)
         return fail(nullptr, TOPO_BADARG, "bad inner solver parameters");
     if (p.homogenize < 0 || p.homogenize > 2) return fail(nullptr, TOPO_BADARG, "homogenize must be 0, 1 or 2");
+    if (p.outer_residual < 0 || p.outer_residual > 1) return fail(nullptr, TOPO_BADARG, "outer_residual must be 0 or 1");
+    if (p.tensor_cores < 0 || p.tensor_cores > 1) return fail(nullptr, TOPO_BADARG, "tensor_cores must be 0 or 1");
     if (p.homogenize == 2 && p.precision == TOPO_MIXED_BF16)
         return fail(nullptr, TOPO_BADARG, "homogenize = 2 (stored Galerkin operators) is not combined with BF16 iterates");
     if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))
@@ -375,6 +381,12 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
         ModalK<float>& b = *h->mk32;
         b.nd = (float)a.nd; b.no = (float)a.no; b.sc = (float)a.sc; b.bp = (float)a.bp; b.bq = (float)a.bq;
         b.td = (float)a.td; b.to = (float)a.to; b.cg = (float)a.cg; b.kdiag = (float)a.kdiag;
+        // double-FP32 pairs: nearest FP32 value and the FP32-rounded remainder
+        auto split = [](double v) { const float hi = (float)v; return dfl(hi, (float)(v - (double)hi)); };
+        h->mkdf = new ModalK<dfl>();
+        ModalK<dfl>& d = *h->mkdf;
+        d.nd = split(a.nd); d.no = split(a.no); d.sc = split(a.sc); d.bp = split(a.bp); d.bq = split(a.bq);
+        d.td = split(a.td); d.to = split(a.to); d.cg = split(a.cg); d.kdiag = split(a.kdiag);
     }
     h->lev.resize(h->L);
     h->npartials = kRedBlocks;
@@ -389,7 +401,8 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
         lv.scale = (double)(1 << l);
         lv.op32 = op_launch32(lv.g, nsm);
         lv.op64 = op_launch64(lv.g, nsm);
-        h->npartials = std::max(h->npartials, std::max(lv.op32.ctas(), lv.op64.ctas()));
+        lv.optc = op_launch_tc(lv.g, nsm);
+        h->npartials = std::max(h->npartials, std::max(lv.op32.ctas(), std::max(lv.op64.ctas(), lv.optc.ctas())));
     }
     topo_status st;
 #define TRY(expr)                          \
@@ -418,6 +431,8 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     TRY(dalloc(h, &h->lam, 8));
     TRY(dalloc(h, &h->dtmp, 8));
     TRY(dalloc(h, &h->dflag, 4));
+    TRY(dalloc(h, &h->tc_err, 1));
+    TRY(dalloc(h, &h->tcB, kTcBWords));
     TRY(dalloc(h, &h->partials, (size_t)h->npartials));
     TRY(dalloc(h, &h->sc, 1));
     h->cs.n = (int)std::min<long long>(3 * h->lev[h->L - 1].g.nn, 1LL << 30);
@@ -432,12 +447,17 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     std::memset(h->host_sc, 0, sizeof(Scalars));
     float K0f[576];
     for (int i = 0; i < 576; ++i) K0f[i] = (float)K0[i];
+    std::vector<uint32_t> tcimg(kTcBWords);
+    tc_b_image(K0, tcimg.data());
     bool ok = cudaMemcpyAsync(h->K0d, K0, sizeof(K0), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
               cudaMemcpyAsync(h->K0f, K0f, sizeof(K0f), cudaMemcpyHostToDevice, h->stream) == cudaSuccess &&
               cudaMemsetAsync(h->x, 0, sizeof(double) * n0, h->stream) == cudaSuccess &&
               cudaMemsetAsync(h->f, 0, sizeof(double) * n0, h->stream) == cudaSuccess &&
               cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream) == cudaSuccess &&
-              cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) == cudaSuccess;
+              cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream) == cudaSuccess &&
+              cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream) == cudaSuccess &&
+              cudaMemcpyAsync(h->tcB, tcimg.data(), sizeof(uint32_t) * kTcBWords, cudaMemcpyHostToDevice,
+                              h->stream) == cudaSuccess;
     for (auto& lv : h->lev) ok = ok && cudaMemsetAsync(lv.mask, 0, lv.g.nn, h->stream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;   // K0 host arrays go out of scope
     if (!ok) {
@@ -548,6 +568,24 @@ topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it, double* 
     s = alloc_precision(h, fp64);
     if (s != TOPO_OK) return s;
     s = ensure_coarse(h);
+    if (s == TOPO_BREAKDOWN) {
+        // the coarsest operator is singular (no or too few Dirichlet
+        // conditions): no iteration ran; the best iterate is the warm start
+        const std::string msg = h->err;
+        const double rel = current_relres(h);
+        if (u_dev_out)
+            CK(h, cudaMemcpyAsync(u_dev_out, h->x, sizeof(double) * 3 * h->lev[0].g.nn, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->stats.inner_iters = 0;
+        h->stats.outer_steps = 0;
+        h->stats.relres = rel;
+        h->stats.status = TOPO_BREAKDOWN;
+        if (iters_out) *iters_out = 0;
+        if (relres_out) *relres_out = rel;
+        h->err = msg;
+        return TOPO_BREAKDOWN;
+    }
     if (s != TOPO_OK) return s;
     int iters = 0;
     double relres = 0.0;
@@ -568,8 +606,14 @@ topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it, double* 
     if (u_dev_out)
         CK(h, cudaMemcpyAsync(u_dev_out, h->x, sizeof(double) * 3 * h->lev[0].g.nn, cudaMemcpyDeviceToDevice,
                               h->stream));
+    int tc_bad = 0;
+    if (h->prm.tensor_cores) CK(h, cudaMemcpyAsync(&tc_bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaGetLastError());
+    if (tc_bad) {
+        cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream);
+        return fail(h, TOPO_CUDA, "tensor-core operator: a bounded wait for the MMA ran out");
+    }
     const auto t1 = std::chrono::steady_clock::now();
     h->stats.inner_iters = iters;
     h->stats.relres = relres;
@@ -733,10 +777,19 @@ topo_status topo_level_dims(topo_handle h, int level, int* nx, int* ny, int* nz)
     return TOPO_OK;
 }
 
-static topo_status step_check(topo_grid* h, int level, int precision, bool allow_bf16 = false) {
+static topo_status step_check(topo_grid* h, int level, int precision, bool allow_bf16 = false,
+                              bool allow_df = false) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
     if (level < 0 || level >= h->L) return fail(h, TOPO_BADARG, "level out of range");
+    if (precision == TOPO_DF32 && allow_df) {
+        if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
+        return alloc_precision(h, true);
+    }
+    if (precision == TOPO_FP32_TC && allow_df) {
+        if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
+        return alloc_precision(h, false);
+    }
     if (precision == TOPO_MIXED_BF16 && allow_bf16) {
         if (!h->have_density) return fail(h, TOPO_BADARG, "set density first");
         s = alloc_precision(h, false);
@@ -752,14 +805,34 @@ static topo_status step_check(topo_grid* h, int level, int precision, bool allow
 enum { OP_APPLY, OP_JACOBI, OP_RESID };
 static topo_status level_op(topo_grid* h, int level, int precision, int op, const double* u, const double* f,
                             double* out) {
-    topo_status s = step_check(h, level, precision);
+    topo_status s = step_check(h, level, precision, false, op != OP_JACOBI || precision == TOPO_FP32_TC);
     if (s != TOPO_OK) return s;
     if (!u || !out || (op != OP_APPLY && !f)) return fail(h, TOPO_BADARG, "NULL pointer");
     const int mode = op == OP_APPLY ? ST_APPLY : (op == OP_JACOBI ? ST_JACOBI : ST_RESID);
     const Ctx c = h->ctx();
     Level& lv = h->lev[level];
     const long long n = 3 * lv.g.nn;
-    if (precision == TOPO_FP64) {
+    if (precision == TOPO_FP32_TC) {
+        if (h->prm.homogenize == 2 && level > 0)
+            return fail(h, TOPO_BADARG, "tensor-core kernel: not for stored Galerkin levels");
+        convert<double, float>(c, n, u, lv.v32.a);
+        if (f) convert<double, float>(c, n, f, lv.v32.f);
+        stencil_tc(c, mode, lv.optc, h->mk32->kdiag, lv.E32, lv.mask, lv.v32.a, f ? lv.v32.f : nullptr, lv.v32.b,
+                   (float)h->prm.omega, h->tcB, nullptr, h->tc_err);
+        convert<float, double>(c, n, lv.v32.b, out);
+        int bad = 0;
+        CK(h, cudaMemcpyAsync(&bad, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (bad) {
+            cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream);
+            return fail(h, TOPO_CUDA, "tensor-core operator: a bounded wait for the MMA ran out");
+        }
+    } else if (precision == TOPO_DF32) {
+        if (h->prm.homogenize == 2 && level > 0)
+            return fail(h, TOPO_BADARG, "double-FP32 kernel: not for stored Galerkin levels");
+        if (stencil_df(c, mode, lv.op64, *h->mkdf, lv.E64, lv.mask, u, f, out, nullptr, nullptr) < 0)
+            return fail(h, TOPO_BADARG, "double-FP32 kernel: mode not available");
+    } else if (precision == TOPO_FP64) {
         op_apply<double>(h, mode, level, u, f, out, nullptr);
     } else {
         convert<double, float>(c, n, u, lv.v32.a);
@@ -873,17 +946,17 @@ topo_status topo_profile_read(topo_handle h, int mode, long long* launches, doub
     if (s != TOPO_OK) return s;
     if (mode < 0 || mode > 3 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
     CK(h, cudaStreamSynchronize(h->stream));
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < 5; ++q) {
         launches[q] = 0;
         total_ms[q] = 0.0;
     }
     for (int i = 0; i < h->prof_n; ++i) {
-        const int k = h->prof_kind[i];   // mode * 4 + precision slot
-        if (k / 4 != mode) continue;
+        const int k = h->prof_kind[i];   // mode * 8 + precision slot
+        if (k / 8 != mode) continue;
         float ms = 0.f;
         CK(h, cudaEventElapsedTime(&ms, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
-        launches[k & 3] += 1;
-        total_ms[k & 3] += ms;
+        launches[k & 7] += 1;
+        total_ms[k & 7] += ms;
     }
     return TOPO_OK;
 }

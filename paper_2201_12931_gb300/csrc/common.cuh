@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "modal.cuh"
 #include "topo.h"
 
@@ -58,6 +59,7 @@ struct Level {
     double* Ke64 = nullptr;   // stored Galerkin element matrices (homogenize = 2, levels >= 1)
     float* Ke32 = nullptr;
     OpLaunch op32, op64;      // operator launch geometry per precision
+    OpLaunch optc;            // tensor-core FP32 operator (tc_op.cu)
     double scale = 1.0;       // 2^l
     double* rho = nullptr;    // homogenized density
     double* E64 = nullptr;    // 2^l * (Emin + rho^p (E0 - Emin))
@@ -107,6 +109,9 @@ struct topo_grid {
     topo::ModalCoef modal{};
     topo::ModalK<double>* mk64 = nullptr;   // host copies of the operator coefficients
     topo::ModalK<float>* mk32 = nullptr;
+    topo::ModalK<topo::dfl>* mkdf = nullptr;  // double-FP32 split of mk64
+    uint32_t* tcB = nullptr;        // B operand image of the tensor-core operator (tc_b_image)
+    int* tc_err = nullptr;          // device: a tensor-core MMA wait ran out (0 = ok)
     long long npartials = 0;                // size of the partials buffer
     double* dc_work = nullptr;      // element work arrays (filter / OC)
     double* xnew_work = nullptr;
@@ -164,6 +169,24 @@ int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, cons
 int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
                  const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
                  double* dot_partials);
+// Operator in double-FP32 arithmetic (dfloat.cuh) on FP64 storage: u, f and
+// the modulus E are FP64, split into FP32 pairs on load; launch geometry of
+// the FP64 kernel.  Instantiated: APPLY -> FP64 out; RESID -> FP64 out; RESID
+// -> FP32 out with r.r partials (the outer residual of the mixed solve).
+// Returns -1 for any other combination, else as stencil().
+int stencil_df(const Ctx& c, int mode, const OpLaunch& L, const ModalK<dfl>& mk, const double* E, const uint8_t* mask,
+               const double* u, const double* f, double* out64, float* out32, double* dot_partials);
+// ---- tc_op.cu: FP32 operators with the element products on tcgen05 tensor cores
+OpLaunch op_launch(const Geom& g, int ty, int target_ctas, int resident_ctas);
+OpLaunch op_launch_tc(const Geom& g, int nsm);
+constexpr int kTcBWords = 2304;
+// host: shared-memory image of B = [K0_hi | K0_lo | K0_hi] (TF32), kTcBWords words
+void tc_b_image(const double* K0, uint32_t* img);
+// APPLY / JACOBI / RESID (with or without dot partials) as stencil(); -1 for
+// JACOBI0.  *err is set if a bounded wait on the tensor cores ran out.
+int stencil_tc(const Ctx& c, int mode, const OpLaunch& L, float kdiag, const float* E, const uint8_t* mask,
+               const float* u, const float* f, float* out, float omega, const uint32_t* Bimg, double* dot_partials,
+               int* err);
 // dense coarsest operator from E_e K0, or from stored element matrices Ke (non-null)
 void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double* E, const double* Ke,
                      const uint8_t* mask, double* A, int npad);

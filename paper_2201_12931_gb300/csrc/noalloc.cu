@@ -51,6 +51,25 @@ topo_status scratch_for_current_device(double** out, std::string* err) {
     return TOPO_OK;
 }
 
+// Neighbour table of radius r written on the device by one thread, in the
+// (dz, dy, dx) order of the host count below: offsets with weight
+// w = r - |d| > 0.  |d|^2 is an integer, so the correctly rounded square root
+// and the comparison give the same table on host and device.
+__global__ void k_filter_table(double r, int R, int4* __restrict__ offs, double* __restrict__ wts) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int n = 0;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                const double w = r - sqrt((double)(dx * dx + dy * dy + dz * dz));
+                if (w > 0.0 && n < kNoAllocMaxOffsets) {
+                    offs[n] = make_int4(dx, dy, dz, 0);
+                    wts[n] = w;
+                    ++n;
+                }
+            }
+}
+
 }  // namespace
 
 }  // namespace topo
@@ -80,26 +99,19 @@ extern "C" topo_status topo_filter_noalloc(int nx, int ny, int nz, double r, con
     double* wts = scratch + 2 * kNoAllocMaxElems;
     int4* offs = reinterpret_cast<int4*>(scratch + 2 * kNoAllocMaxElems + kNoAllocMaxOffsets);
 
-    // neighbour table of the radius, on the stack (no heap either)
-    int4 h_offs[kNoAllocMaxOffsets];
-    double h_wts[kNoAllocMaxOffsets];
+    // the neighbour table is written on the device (k_filter_table); the
+    // host only counts its entries, so no host memory is copied and the
+    // launches depend on the arguments alone
     int n = 0;
     const int R = (int)std::ceil(r);
     for (int dz = -R; dz <= R; ++dz)
         for (int dy = -R; dy <= R; ++dy)
-            for (int dx = -R; dx <= R; ++dx) {
-                const double w = r - std::sqrt((double)(dx * dx + dy * dy + dz * dz));
-                if (w > 0.0 && n < kNoAllocMaxOffsets) {
-                    h_offs[n] = make_int4(dx, dy, dz, 0);
-                    h_wts[n] = w;
-                    ++n;
-                }
-            }
+            for (int dx = -R; dx <= R; ++dx)
+                if (r - std::sqrt((double)(dx * dx + dy * dy + dz * dz)) > 0.0 && n < kNoAllocMaxOffsets) ++n;
     cudaStream_t s = (cudaStream_t)stream;
-    // pageable-memory copies return once the source has been staged
-    cudaError_t e = cudaMemcpyAsync(offs, h_offs, sizeof(int4) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(wts, h_wts, sizeof(double) * n, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(TOPO_CUDA, std::string("copy of the filter table: ") + cudaGetErrorString(e));
+    k_filter_table<<<1, 32, 0, s>>>(r, R, offs, wts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TOPO_CUDA, std::string("filter table launch: ") + cudaGetErrorString(e));
 
     long long launches = 0;
     const Ctx c{s, &launches};

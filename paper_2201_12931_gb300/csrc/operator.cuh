@@ -24,8 +24,20 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace topo {
+
+// storage type of the modulus and right-hand side read by the operator
+// kernel for arithmetic type T (double-FP32 arithmetic reads FP64 arrays)
+template <typename T>
+struct OpStore {
+    using type = T;
+};
+template <>
+struct OpStore<dfl> {
+    using type = double;
+};
 
 template <typename T>
 struct ModalK {           // structure verified on the host (build_modal_k)
@@ -121,9 +133,12 @@ __device__ __forceinline__ void face_inverse(const T* A, T* c00, T* c10, T* c01,
 }
 
 // element: bottom face modes FB, top face modes FT (12 each), modulus E ->
-// modal outputs folded back to face space: Bo (bottom), To (top)
+// modal outputs folded back to face space: Bo (bottom), To (top).  zc (3,
+// optional): added to the z-difference of the mean mode (modes 12..14) when
+// the two faces were shifted by different translations.
 template <typename T>
-__device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* FB, const T* FT, T* Bo, T* To) {
+__device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* FB, const T* FT, T* Bo, T* To,
+                                              const T* zc = nullptr) {
     T m[24];
     if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
@@ -141,6 +156,10 @@ __device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* 
                 m[3 * g + c] = FT[3 * g + c] + FB[3 * g + c];
                 m[3 * (g + 4) + c] = FT[3 * g + c] - FB[3 * g + c];
             }
+    }
+    if (zc) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) m[12 + c] = m[12 + c] + zc[c];
     }
     const T nd = E * k.nd, no = E * k.no, sc = E * k.sc, bp = E * k.bp, bq = E * k.bq;
     const T td = E * k.td, to = E * k.to, cg = E * k.cg;

@@ -15,4 +15,6 @@ int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot);
 int vcycle_bf16(topo_grid* h, int l, const float* f, float* out, double* dot);
 int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres);
 int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres);
+// ||f - K x|| / ||f|| of the current iterate in FP64 (1 when x is known to be 0)
+double current_relres(topo_grid* h);
 }  // namespace topo

@@ -1,6 +1,6 @@
-// Matrix-free element-by-element operator (Sec. 4.2.1: "sum of density times
-// local stiffness matrices of these 8 elements gives the value equal to global
-// stiffness value of that node"), fused with the damped Jacobi sweep
+// Matrix-free element-by-element operator (Sec. 4.2.1: a node's row of K is
+// the modulus-weighted sum of the reference element matrix over the 8
+// elements around it), fused with the damped Jacobi sweep
 // (Sec. 3.2) and the residual (Eq. residual); coarse-grid assembly; element
 // energy and compliance sensitivity (Eq. sensitivity).
 //
@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "modal.cuh"
 #include "operator.cuh"
+#include "opio.cuh"
 
 namespace topo {
 
@@ -29,37 +30,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return t;   // valid in thread 0
 }
 
-// Shared-memory slots hold one node's three components padded to four, so a
-// slot moves with one 128-bit access (FP32) or a 128 + 64-bit pair (FP64).
-__device__ __forceinline__ void st3(float* p, const float* v) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
-}
-__device__ __forceinline__ void ld3(const float* p, float* v) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = a.z;
-}
-__device__ __forceinline__ void st3(double* p, const double* v) {
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-    p[2] = v[2];
-}
-__device__ __forceinline__ void ld3(const double* p, double* v) {
-    const double2 a = *reinterpret_cast<const double2*>(p);
-    v[0] = a.x;
-    v[1] = a.y;
-    v[2] = p[2];
-}
-// vector element loads / stores with widening from and rounding to the
-// storage type (BF16 iterates of the V-cycle; arithmetic stays in T)
-__device__ __forceinline__ float ldv(const float* p) { return *p; }
-__device__ __forceinline__ double ldv(const double* p) { return *p; }
-__device__ __forceinline__ float ldv(const bf16* p) { return __bfloat162float(*p); }
-__device__ __forceinline__ void stv(float* p, float v) { *p = v; }
-__device__ __forceinline__ void stv(double* p, double v) { *p = v; }
-__device__ __forceinline__ void stv(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Element-column z-march operator kernel; see operator.cuh for the scheme.
 // The per-plane body is a generic lambda called with a compile-time buffer
@@ -68,9 +38,9 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // T: arithmetic, f, E; TU: storage of u; TO: storage of the output.
 template <typename T, typename TU, typename TO, int MODE, bool DOT>
 __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
-    k_op(const ModalK<T> mk, const T* __restrict__ E, const uint8_t* __restrict__ mask, const TU* __restrict__ u,
-         const T* __restrict__ f, TO* __restrict__ out, const int nx, const int ny, const int nz, const int cz,
-         const T omega, double* __restrict__ partials) {
+    k_op(const ModalK<T> mk, const typename OpStore<T>::type* __restrict__ E, const uint8_t* __restrict__ mask,
+         const TU* __restrict__ u, const typename OpStore<T>::type* __restrict__ f, TO* __restrict__ out,
+         const int nx, const int ny, const int nz, const int cz, const T omega, double* __restrict__ partials) {
     constexpr int TX = kOpTX, TY = op_ty<T>();
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
     constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
@@ -78,6 +48,19 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     constexpr int nU = (TY + 1) * (TX + 1) * 4, nC = 3 * TY * TX * 4, nEs = TY * TX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
+    // double-FP32 arithmetic: the node values of each plane are shifted by
+    // that plane's value at the tile's corner node (in FP64, before the
+    // split), so that the FP32 pairs carry the displacement relative to the
+    // tile rather than its absolute size.  K annihilates a translation, and
+    // within a plane the shift is one; between the two planes of an element
+    // it leaves only the z-difference of the mean mode, which is added back
+    // (4 (ref_P - ref_{P-1}) in element_modal).  Thread 0 keeps the last
+    // reference (sref_last) and publishes the split correction of each plane
+    // in a ring of four slots (szc).
+    constexpr bool kDF = std::is_same<T, dfl>::value;
+    __shared__ double sref_last[4];
+    __shared__ __align__(16) float szc[4][8];
+    if (kDF && threadIdx.x == 0 && threadIdx.y == 0) sref_last[0] = sref_last[1] = sref_last[2] = 0.0;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int NX = nx + 1, NY = ny + 1;
@@ -107,51 +90,75 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     T st00[3] = {}, st10[3] = {}, st01[3] = {}, st11[3] = {};
     T stE = T(0);
     double dot = 0.0;
+    [[maybe_unused]] float dotf = 0.0f;
     // per-plane register slots, slot = plane & 3: own node raw u, f, mask,
     // the column modulus of the layer below the plane, and (two slots) the
-    // halo node; planes P-2 .. P+1 are live in step P, so no copies occur
-    T su[4][3], sf[4][3], sE[4];
+    // halo node; planes P-2 .. P+1 are live in step P, so no copies occur.
+    // Double-FP32 arithmetic keeps the loaded FP64 words in the slots and
+    // splits them where they are used (a load is never consumed in the step
+    // that issues it), and fetches f only one step ahead of its use.
+    using TSl = std::conditional_t<kDF, double, T>;
+    TSl su[4][3], sf[4][3], sE[4];
     unsigned sm[4];
-    T shv[2][3];
+    TSl shv[2][3];
     unsigned shm[2];
+    [[maybe_unused]] double srf[2][3];   // plane references (double-FP32)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        su[q][0] = su[q][1] = su[q][2] = T(0);
-        sf[q][0] = sf[q][1] = sf[q][2] = T(0);
-        sE[q] = T(0);
+        su[q][0] = su[q][1] = su[q][2] = TSl(0);
+        sf[q][0] = sf[q][1] = sf[q][2] = TSl(0);
+        sE[q] = TSl(0);
         sm[q] = 0u;
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        shv[q][0] = shv[q][1] = shv[q][2] = T(0);
+        shv[q][0] = shv[q][1] = shv[q][2] = TSl(0);
         shm[q] = 0u;
+        srf[q][0] = srf[q][1] = srf[q][2] = 0.0;
     }
     const int own3 = 3 * own_xy, halo3 = 3 * halo_xy;
+    [[maybe_unused]] const int ref3 = 3 * (i0 + NX * j0);   // tile corner node (always in the grid)
 
     // load plane P into slot S (plane-uniform base + per-thread offset)
     auto fetch = [&](auto Sc, int P) {
         constexpr int S = decltype(Sc)::value;
         const bool pin = P >= 0 && P <= nz;
         const long long pb = (long long)P * nplane;
-        if (NEEDU || NEEDF) {
+        if constexpr (kDF) {
+            // raw FP64 words: own and halo node, the plane's reference (tile
+            // corner node); f is loaded by the step (one plane behind)
             const bool ok = pin && node_ok;
             sm[S] = ok ? mask[pb + own_xy] : 0u;
             const TU* ub = u + 3 * pb + own3;
-            const T* fb_ = f + 3 * pb + own3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                su[S][c] = ok ? (double)ub[c] : 0.0;
+                srf[S & 1][c] = pin ? (double)u[3 * pb + ref3 + c] : 0.0;
+            }
+            const bool okh = pin && halo_ok;
+            shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
+            const TU* hb = u + 3 * pb + halo3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (double)hb[c] : 0.0;
+        } else if (NEEDU || NEEDF) {
+            const bool ok = pin && node_ok;
+            sm[S] = ok ? mask[pb + own_xy] : 0u;
+            const TU* ub = u + 3 * pb + own3;
+            const typename OpStore<T>::type* fb_ = f + 3 * pb + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 if (NEEDU) su[S][c] = ok ? (T)ldv(ub + c) : T(0);
-                if (NEEDF) sf[S][c] = ok ? fb_[c] : T(0);
+                if (NEEDF) sf[S][c] = ok ? (T)fb_[c] : T(0);
             }
         }
-        if (NEEDU) {
+        if constexpr (NEEDU && !kDF) {
             const bool okh = pin && halo_ok;
             shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
             const TU* hb = u + 3 * pb + halo3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
         }
-        sE[S] = (col_ok && P >= 1 && P <= nz) ? E[(long long)(P - 1) * nx * ny + col_xy] : T(0);
+        sE[S] = (col_ok && P >= 1 && P <= nz) ? (TSl)E[(long long)(P - 1) * nx * ny + col_xy] : TSl(0);
     };
 
     // step of node plane P, B = P & 3 (static)
@@ -160,12 +167,35 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
         constexpr int B2 = B & 1;                 // shared-memory buffer
         constexpr int SN = (B + 1) & 3;           // slot of plane P + 1
         constexpr int SO = (B + 2) & 3;           // slot of plane P - 2 (output)
-        constexpr int SL = (B + 3) & 3;           // slot of plane P - 1
+        [[maybe_unused]] constexpr int SL = (B + 3) & 3;   // slot of plane P - 1
         T* const U = reinterpret_cast<T*>(smem_raw) + B2 * nU;
         T* const Cb = reinterpret_cast<T*>(smem_raw) + 2 * nU + B2 * nC;
-        T* const Eb = reinterpret_cast<T*>(smem_raw) + 2 * nU + 2 * nC + B2 * nEs;
+        [[maybe_unused]] T* const Eb = reinterpret_cast<T*>(smem_raw) + 2 * nU + 2 * nC + B2 * nEs;
         // publish plane P (masked) and the stashed contributions of plane P - 2
-        if (NEEDU) {
+        if constexpr (kDF) {
+            // masked, shifted by the plane reference in FP64, then split
+            const unsigned cm = sm[B];
+            T mu[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mu[c] = T((((cm >> c) & 1u) ? 0.0 : su[B][c]) - srf[B & 1][c]);
+            if (tid == 0) {   // correction of the element between planes P - 1 and P
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const dfl d = df_from_double(srf[B & 1][c] - sref_last[c]);
+                    szc[B][2 * c] = 4.0f * d.h;   // exact: a power of two
+                    szc[B][2 * c + 1] = 4.0f * d.l;
+                    sref_last[c] = srf[B & 1][c];
+                }
+            }
+            st3(U + uoff, mu);
+            if (has_halo) {
+                const unsigned chm = shm[B & 1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    mu[c] = T((((chm >> c) & 1u) ? 0.0 : shv[B & 1][c]) - srf[B & 1][c]);
+                st3(U + hoff, mu);
+            }
+        } else if (NEEDU) {
             const unsigned cm = sm[B];
             T mu[3] = {su[B][0], su[B][1], su[B][2]};
             if (cm) {
@@ -183,9 +213,16 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
             st3(Cb + nC / 3 + coff, st01);
             st3(Cb + 2 * (nC / 3) + coff, st11);
         }
-        if (NEEDD) Eb[ty * TX + tx] = stE;
+        if constexpr (NEEDD) Eb[ty * TX + tx] = stE;
         // start loading plane P + 1 (its slot held plane P - 3, no longer needed)
         if (P + 1 <= kz1) fetch(std::integral_constant<int, SN>{}, P + 1);
+        if constexpr (kDF && NEEDF) {
+            // f of plane P - 1, output by the next step (slot SL is not read here)
+            const bool okf = P - 1 >= 0 && P - 1 <= nz && node_ok;
+            const double* ff = f + 3 * ((long long)(P - 1) * nplane) + own3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sf[SL][c] = okf ? ff[c] : 0.0;
+        }
         __syncthreads();
         // output node plane Q = P - 2
         const int Q = P - 2;
@@ -199,26 +236,32 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
             }
-            T rD = T(1);
-            if (NEEDD) {
+            [[maybe_unused]] T rD = T(1);
+            if constexpr (NEEDD) {
                 const T* e = Eb + ty * TX + tx;
                 rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
             TO* o = out + 3 * ((long long)Q * nplane) + own3;
             const unsigned m2 = sm[SO];
-            T d32 = T(0);
+            typename DotAcc<T>::type d32 = 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const bool fixed = (m2 >> c) & 1u;
-                const T uo = su[SO][c], fo = sf[SO][c];
+                [[maybe_unused]] T uo;
+                [[maybe_unused]] const T fo = T(sf[SO][c]);
+                if constexpr (kDF) {   // fixed rows read u itself (the slots are not kept)
+                    uo = fixed ? T((double)u[3 * ((long long)Q * nplane) + own3 + c]) : T(0);
+                } else {
+                    uo = su[SO][c];
+                }
                 T r;
-                if (MODE == ST_APPLY) {
+                if constexpr (MODE == ST_APPLY) {
                     r = fixed ? uo : y[c];
-                    if (DOT) d32 += uo * r;
-                } else if (MODE == ST_RESID) {
+                    if (DOT) d32 += to_acc(uo) * to_acc(r);
+                } else if constexpr (MODE == ST_RESID) {
                     r = fo - (fixed ? uo : y[c]);
-                    if (DOT) d32 += r * r;
-                } else if (MODE == ST_JACOBI) {
+                    if (DOT) d32 += to_acc(r) * to_acc(r);
+                } else if constexpr (MODE == ST_JACOBI) {
                     r = fixed ? uo + omega * (fo - uo) : uo + omega * (fo - y[c]) * rD;
                     if (DOT) d32 += fo * r;
                 } else {
@@ -227,7 +270,10 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 }
                 stv(o + c, r);
             }
-            if (DOT) dot += (double)d32;
+            if constexpr (DOT) {
+                if constexpr (kDF) dotf += d32;   // FP32 per thread, FP64 across threads
+                else dot += (double)d32;
+            }
         }
         // face modes of plane P; element of layer P - 1; plane P - 1 completes
         if (P >= kz0 && P <= kz1) {
@@ -239,7 +285,14 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 ld3(U + uoff + (TX + 1) * 4 + 4, c11);
                 face_forward<T>(c00, c10, c01, c11, fb[B2]);
                 T Bo[12], To[12];
-                element_modal<T>(mk, sE[B], fb[B2 ^ 1], fb[B2], Bo, To);
+                if constexpr (kDF) {
+                    T zc[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) zc[c] = T(szc[B][2 * c], szc[B][2 * c + 1]);
+                    element_modal<T>(mk, T(sE[B]), fb[B2 ^ 1], fb[B2], Bo, To, zc);
+                } else {
+                    element_modal<T>(mk, sE[B], fb[B2 ^ 1], fb[B2], Bo, To);
+                }
                 T A[12];
 #pragma unroll
                 for (int i = 0; i < 12; ++i) {
@@ -247,8 +300,17 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                     top[i] = To[i];
                 }
                 face_inverse<T>(A, st00, st10, st01, st11);
+                if constexpr (kDF) {
+                    // contributions to the neighbours' corners of plane P - 1 go
+                    // straight to the buffer the next step's output reads (every
+                    // thread has passed this step's barrier, so nobody reads it)
+                    T* const Cn = reinterpret_cast<T*>(smem_raw) + 2 * nU + (B2 ^ 1) * nC;
+                    st3(Cn + coff, st10);
+                    st3(Cn + nC / 3 + coff, st01);
+                    st3(Cn + 2 * (nC / 3) + coff, st11);
+                }
             }
-            if (NEEDD) stE = sE[SL] + sE[B];
+            if constexpr (NEEDD) stE = sE[SL] + sE[B];
         } else if (NEEDU && P == kz0 - 1) {
             T c00[3], c10[3], c01[3], c11[3];
             ld3(U + uoff, c00);
@@ -280,7 +342,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
         step(S3{}, P + 3);
     }
     if (DOT) {
-        double v = dot;
+        double v = kDF ? (double)dotf : dot;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int w = tid >> 5, l = tid & 31;
         if (l == 0) sred[w] = v;
@@ -300,8 +362,8 @@ constexpr size_t op_smem_bytes() {
 }
 
 template <typename T, int MODE, bool DOT, typename TU = T, typename TO = T>
-void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const TU* u,
-               const T* f, TO* out, T omega, double* dot) {
+void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const typename OpStore<T>::type* E,
+               const uint8_t* mask, const TU* u, const typename OpStore<T>::type* f, TO* out, T omega, double* dot) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_op<T, TU, TO, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -500,6 +562,21 @@ int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>&
         else launch_op<float, ST_JACOBI, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
     } else if (mode == ST_RESID && out_f && !dot) {
         launch_op<float, ST_RESID, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
+    } else {
+        return -1;   // combination not instantiated
+    }
+    return dot ? L.gx * L.gy * L.gz : 0;
+}
+
+int stencil_df(const Ctx& c, int mode, const OpLaunch& L, const ModalK<dfl>& mk, const double* E, const uint8_t* mask,
+               const double* u, const double* f, double* out64, float* out32, double* dot) {
+    const dfl om(0.0f, 0.0f);   // no damping in these modes
+    if (mode == ST_APPLY && out64 && !dot) {
+        launch_op<dfl, ST_APPLY, false, double, double>(c, L, mk, E, mask, u, nullptr, out64, om, nullptr);
+    } else if (mode == ST_RESID && out64 && !dot) {
+        launch_op<dfl, ST_RESID, false, double, double>(c, L, mk, E, mask, u, f, out64, om, nullptr);
+    } else if (mode == ST_RESID && out32 && dot) {
+        launch_op<dfl, ST_RESID, true, double, float>(c, L, mk, E, mask, u, f, out32, om, dot);
     } else {
         return -1;   // combination not instantiated
     }

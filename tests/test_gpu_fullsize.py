@@ -2,7 +2,8 @@
 
 * 768x384x384 cantilever (113M elements, the bench workload's grid and 7
   levels): operator rows at sampled nodes (random, corners, clamped face,
-  loaded edge, CTA tile seams) on levels 0, 1 and 3, FP64 and FP32 kernels,
+  loaded edge, CTA tile seams) on levels 0, 1 and 3, FP64, FP32 and
+  double-FP32 kernels,
   against the oracle evaluating the same rows from local data
   (oracle.assemble.operator_rows).  Inputs are drawn from the counter-based
   generator, so the oracle reads the density and vector entries it needs
@@ -87,11 +88,13 @@ def test_operator_rows_at_sampled_nodes(big_grid, level):
     u = torch.tensor(synth.uniform01(seed, 3 * nn_l) - 0.5, device=cuda_device())
     y64 = g.apply_operator(u, level=level, precision=0)
     y32 = g.apply_operator(u, level=level, precision=1)
+    ydf = g.apply_operator(u, level=level, precision=3)
     nodes = _sample_nodes(dims_l, 300, 45 + level)
     idx = torch.tensor((3 * nodes[:, None] + np.arange(3)).ravel(), device=cuda_device())
     g64 = n(y64[idx]).reshape(-1, 3)
     g32 = n(y32[idx]).reshape(-1, 3)
-    del u, y64, y32
+    gdf = n(ydf[idx]).reshape(-1, 3)
+    del u, y64, y32, ydf
     K0 = element.element_stiffness(0.3)
     ref = assemble.operator_rows(dims_l, nodes, _coarse_E(level, dims_l),
                                  lambda d: synth.uniform01_at(seed, d) - 0.5, K0,
@@ -99,6 +102,7 @@ def test_operator_rows_at_sampled_nodes(big_grid, level):
     scale = np.abs(ref).max()
     assert np.abs(g64 - ref).max() <= 1e-12 * scale
     assert np.abs(g32 - ref).max() <= 1e-5 * scale
+    assert np.abs(gdf - ref).max() <= 1e-12 * scale
 
 
 def test_mixed_solve_compliance_against_fp64(big_grid):

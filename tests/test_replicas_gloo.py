@@ -69,9 +69,11 @@ def test_reference_arm_prints_on_rank0_only(monkeypatch, capsys):
 
 def test_roofline_entries():
     """The bench line's roofline objects: HBM-bound FP32 kernels against the
-    measured copy bandwidth, the FP64 residual against the derived FP64 peak."""
+    measured copy bandwidth, the FP64 and double-FP32 residuals against the
+    measured FP64 / FP32 FMA peaks (stand-in values here: no GPU)."""
     sys.path.insert(0, ROOT)
     import bench
+    bench._ALU.update(fp64=1.1, fp32=61.0, fp32x2=63.0)
     ne = 1000
     r32 = {"mode": 0, "prec": 1, "kernel": "K.u (fp32) fine level", "launches": 3, "avg_launch_ms": 0.5,
            "algorithmic_bytes_per_launch": 2e9, "achieved_gbs": 4000.0, "frac": 0.6}
@@ -83,7 +85,12 @@ def test_roofline_entries():
     tflops = bench.MODAL_FLOPS_PER_ELEMENT * ne / 1e-3 / 1e12
     assert e["bound"] == "alu" and e["unit"] == "TFLOP/s" and e["traffic"] is None
     assert abs(e["achieved"] - round(tflops, 4)) < 1e-9
-    assert abs(e["peak"] - 152 * 4 * 2.07e9 / 1e12) < 1e-3
+    assert e["peak"] == 1.1 and e["peak_source"].startswith("measured")
+    rdf = {"mode": 2, "prec": 3, "kernel": "residual (double-fp32) fine level", "launches": 2, "avg_launch_ms": 0.5,
+           "algorithmic_bytes_per_launch": 1e9, "achieved_gbs": 2000.0, "frac": 0.3}
+    e = bench.roofline_entry(rdf, 6700.0, "measured", ne)
+    assert e["bound"] == "alu" and e["peak"] == 63.0
+    assert abs(e["achieved"] - round(bench.DF_FLOPS_PER_ELEMENT * ne / 0.5e-3 / 1e12, 4)) < 1e-9
     # the dominant kernel is the one with the largest total time
     rows = [dict(r32, total_ms=1.5), dict(r64, total_ms=2.0)]
     assert bench.roofline(rows, 6700.0, "measured", ne)["bound"] == "alu"
@@ -92,6 +99,7 @@ def test_roofline_entries():
     nn = 100
     assert bench.op_bytes(1, 2, nn, ne) == 3 * nn * (2 + 4 + 2) + 4 * ne
     assert bench.op_bytes(1, 1, nn, ne) == 3 * 3 * nn * 4 + 4 * ne
+    assert bench.op_bytes(2, 3, nn, ne) == 3 * nn * (8 + 8 + 4) + 8 * ne
 
 
 def test_bench_defaults_follow_the_contract():
