@@ -56,12 +56,21 @@ def parse_args(argv=None):
     ap.add_argument("--graphs", choices=["on", "off"], default="on",
                     help="replay PCG iterations from captured CUDA graphs (off: direct launches)")
     ap.add_argument("--oc-iters", type=int, default=0, help="OC loop: iterations (default: the workload's)")
+    ap.add_argument("--cg-check", choices=["batched", "every"], default="batched",
+                    help="host reads of r.r: after batches sized from the contraction rate, or every CG iteration")
+    ap.add_argument("--sweeps", default="2,2", help="Jacobi sweeps before,after the coarse correction")
+    ap.add_argument("--tensor-cores", choices=["off", "on"], default="off",
+                    help="FP32 operators with tcgen05 element products instead of the modal kernel")
     ap.add_argument("--oc-fp64", choices=["on", "off"], default="on",
                     help="OC loop: also run the all-FP64 loop for the drift comparison")
     ap.add_argument("--oc-loop", action="store_true",
                     help="run the workload's topology-optimisation loop (mixed and FP64) instead of the step bench")
     ap.add_argument("--oracle-table", choices=["on", "off"], default="on",
                     help="time the oracle and the GPU path on the small configurations (C1-C3) in the same run")
+    ap.add_argument("--traffic-from", default=None,
+                    help="write profiles/traffic.json from an ncu CSV of dram__bytes_{read,write}.sum of the "
+                         "operator kernels of a run with --dims (see profiles/traffic.json for the command)")
+    ap.add_argument("--traffic-command", default="", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -405,7 +414,66 @@ def kernel_table(grid, nn, ne):
     return rows, peak, src
 
 
-KERNEL_SOURCES = ["paper_2201_12931_gb300/csrc/stencil.cu", "paper_2201_12931_gb300/csrc/operator.cuh"]
+KERNEL_SOURCES = ["paper_2201_12931_gb300/csrc/stencil.cu", "paper_2201_12931_gb300/csrc/operator.cuh",
+                  "paper_2201_12931_gb300/csrc/opio.cuh", "paper_2201_12931_gb300/csrc/dfloat.cuh",
+                  "paper_2201_12931_gb300/csrc/tc_op.cu"]
+
+
+def kernel_kind(name):
+    """(mode, prec) of an operator kernel from its demangled ncu name, else None:
+    k_op<T, TU, TO, MODE, DOT> (T float / double / dfl, TU bf16 for BF16
+    iterates) and k_op_tc<MODE, DOT>."""
+    import re
+    m = re.search(r"k_op_tc<(?:\(int\))?(\d), (?:\(bool\))?(\d)>", name)
+    if m:
+        return int(m.group(1)), 4
+    m = re.search(r"k_op<([^,]+), ([^,]+), ([^,]+), (?:\(int\))?(\d), (?:\(bool\))?(\d)>", name)
+    if not m:
+        return None
+    t, tu = m.group(1).strip(), m.group(2).strip()
+    prec = 3 if "dfl" in t else (0 if t == "double" else (2 if "bfloat16" in tu else 1))
+    return int(m.group(4)), prec
+
+
+def write_traffic(args):
+    """Fine-level launches (largest grid of each kind) of an ncu CSV with
+    dram__bytes_read.sum / dram__bytes_write.sum -> profiles/traffic.json."""
+    import csv
+    _, dims, _ = workload(args)
+    launches = {}
+    with open(args.traffic_from) as fh:
+        rows = [r for r in csv.reader(fh) if len(r) > 10]
+    hdr = rows[0]
+    ix = {k: hdr.index(k) for k in ("ID", "Kernel Name", "Grid Size", "Metric Name", "Metric Unit", "Metric Value")}
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6}
+    for r in rows[1:]:
+        kind = kernel_kind(r[ix["Kernel Name"]])
+        if kind is None:
+            continue
+        d = launches.setdefault(r[ix["ID"]], {"kind": kind, "grid": r[ix["Grid Size"]], "name": r[ix["Kernel Name"]]})
+        d[r[ix["Metric Name"]]] = float(r[ix["Metric Value"]].replace(",", "")) * scale.get(r[ix["Metric Unit"]], 1)
+    def volume(g):
+        return eval(g.replace("(", "").replace(")", "").replace(",", "*"))
+    best = {}
+    for d in launches.values():
+        if "dram__bytes_read.sum" not in d:
+            continue
+        k = d["kind"]
+        if k not in best or volume(d["grid"]) > volume(best[k]["grid"]):
+            best[k] = d
+    entries = [{"mode": k[0], "prec": k[1], "kernel": d["name"].split("(")[0].replace("void ", "")[:120],
+                "dims": list(dims), "grid": d["grid"], "dram_bytes_read": int(d["dram__bytes_read.sum"]),
+                "dram_bytes_write": int(d["dram__bytes_write.sum"]),
+                "duration_ns": int(d.get("gpu__time_duration.sum", 0))} for k, d in sorted(best.items())]
+    out = {"kernel_sha256": kernel_hash(), "command": args.traffic_command,
+           "note": (f"first fine-level launch (largest grid) of each operator kernel kind on the {dims[0]}x{dims[1]}x"
+                    f"{dims[2]} grid; bench.py scales the bytes to the workload by element count (the operator "
+                    "kernels stream the fine-level vectors once per launch, so traffic grows with the elements); "
+                    "durations are cold-cache and serialised under ncu"),
+           "entries": entries}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out, indent=1))
 
 
 def kernel_hash():
@@ -535,7 +603,10 @@ def run_ours(args):
     move = w.get("oc", {}).get("move", 0.2)
 
     hom = COARSENING[args.coarsening]
-    g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom, graphs=int(args.graphs == "on")))
+    pre, post = (int(v) for v in args.sweeps.split(","))
+    g = TopoGrid(dims, Params(levels=levels, precision=prec, homogenize=hom, graphs=int(args.graphs == "on"),
+                              cg_check=int(args.cg_check == "every"), tensor_cores=int(args.tensor_cores == "on"),
+                              pre=pre, post=post))
     rho0 = physical_density(g, args.workload, dims, dev)
     volfrac = w.get("oc", {}).get("volfrac", float(rho0.mean()))
     g.set_bc_loads(fixed_d, f_d)
@@ -621,6 +692,7 @@ def run_ours(args):
         "config": {"workload": args.workload if not args.dims else f"{args.workload}@{nx}x{ny}x{nz}",
                    "grid": f"{nx}x{ny}x{nz}", "elements": ne, "dofs": 3 * nn, "levels": levels,
                    "rel_tol": args.rel_tol, "precision": w["precision"], "coarsening": args.coarsening,
+                   "sweeps": args.sweeps,
                    "l2": "inputs larger than L2 (fine-level vectors >= 129 MB)" if 12 * nn > 129e6
                    else "inputs smaller than L2 (no flush)"},
         "solve": {"status": res_last.status, "inner_iters": res_last.iters, "outer_steps": res_last.outer_steps,
@@ -713,7 +785,7 @@ def run_oc_loop(args):
         prec, plabel = TOPO_MIXED, "mixed"
     tol = w.get("rel_tol", 1e-8)
     out = {"mode": "oc_loop", "workload": name, "grid": "x".join(map(str, dims)), "levels": levels,
-           "rel_tol": tol, "graphs": args.graphs, "rmin": oc["rmin"], "move": oc["move"],
+           "rel_tol": tol, "graphs": args.graphs, "cg_check": args.cg_check, "rmin": oc["rmin"], "move": oc["move"],
            "volfrac": oc["volfrac"], "coarsening": args.coarsening, "filter": args.filter}
     bridge = w.get("bridge")
     flt = "sensitivity" if bridge else args.filter     # non-design regions: the paper's scheme
@@ -727,7 +799,8 @@ def run_oc_loop(args):
     runs = {}
     for label, p in (("mixed", prec), ("fp64", TOPO_FP64))[:2 if args.oc_fp64 == "on" else 1]:
         g = TopoGrid(dims, Params(levels=levels, precision=p, homogenize=COARSENING[args.coarsening],
-                                  graphs=int(args.graphs == "on")))
+                                  graphs=int(args.graphs == "on"), cg_check=int(args.cg_check == "every"),
+                                  tensor_cores=int(args.tensor_cores == "on")))
         g.set_bc_loads(fixed_d, f_d)
         x = x0.clone()
         dc = torch.empty(ne, dtype=torch.float64, device=dev)
@@ -794,7 +867,9 @@ def run_reference(args):
 
 def main():
     args = parse_args()
-    if args.cpu_child:
+    if args.traffic_from:
+        write_traffic(args)
+    elif args.cpu_child:
         run_cpu_child(args)
     elif args.oracle_child:
         run_oracle_child(args.oracle_child)

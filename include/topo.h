@@ -102,6 +102,9 @@ typedef struct {
                         /* 1 = element products K0 (u_e - u_e0) on the tcgen05    */
                         /* tensor cores, TF32 operands split hi + lo (about 22    */
                         /* bits), FP32 accumulation in tensor memory              */
+    int cg_check;       /* 0: the host reads r.r after batches of CG iterations   */
+                        /* sized from the observed contraction rate (at most 8;   */
+                        /* default); 1: after every iteration                     */
 } topo_params;
 
 /* Fills *p with the defaults listed above.  TOPO_BADARG if p is NULL. */

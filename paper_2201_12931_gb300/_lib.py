@@ -23,7 +23,8 @@ class TopoParams(C.Structure):
                 ("levels", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("omega", C.c_double),
                 ("precision", C.c_int), ("inner_tol", C.c_double), ("inner_max_it", C.c_int),
                 ("max_refine", C.c_int), ("homogenize", C.c_int), ("graphs", C.c_int),
-                ("outer_residual", C.c_int), ("tensor_cores", C.c_int)]
+                ("outer_residual", C.c_int), ("tensor_cores", C.c_int),
+                ("cg_check", C.c_int)]
 
 
 class TopoSolveStats(C.Structure):

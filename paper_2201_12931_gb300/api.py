@@ -39,6 +39,7 @@ class Params:
     graphs: int = 1
     outer_residual: int = 0
     tensor_cores: int = 0
+    cg_check: int = 0
 
     def to_c(self) -> L.TopoParams:
         p = L.TopoParams()

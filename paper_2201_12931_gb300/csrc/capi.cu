@@ -326,6 +326,7 @@ topo_status topo_default_params(topo_params* p) {
     p->graphs = 1;
     p->outer_residual = 0;
     p->tensor_cores = 0;
+    p->cg_check = 0;
     return TOPO_OK;
 }
 
@@ -350,6 +351,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     if (p.homogenize < 0 || p.homogenize > 2) return fail(nullptr, TOPO_BADARG, "homogenize must be 0, 1 or 2");
     if (p.outer_residual < 0 || p.outer_residual > 1) return fail(nullptr, TOPO_BADARG, "outer_residual must be 0 or 1");
     if (p.tensor_cores < 0 || p.tensor_cores > 1) return fail(nullptr, TOPO_BADARG, "tensor_cores must be 0 or 1");
+    if (p.cg_check < 0 || p.cg_check > 1) return fail(nullptr, TOPO_BADARG, "cg_check must be 0 or 1");
     if (p.homogenize == 2 && p.precision == TOPO_MIXED_BF16)
         return fail(nullptr, TOPO_BADARG, "homogenize = 2 (stored Galerkin operators) is not combined with BF16 iterates");
     if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))

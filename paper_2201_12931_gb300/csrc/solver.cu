@@ -332,6 +332,16 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
     const bool use_graph = h->prm.graphs != 0 && !h->prof_on && !gr.failed;
     step_a();
     int it = 1;
+    // The host reads r.r (one stream synchronisation) after a batch of
+    // iterations: one at a time for the first two, then as many as the
+    // observed contraction rate predicts are still needed (at most 8, and
+    // rounded down so that the batch does not step past the target while
+    // the rate holds).  topo_params.cg_check = 1 reads after every iteration.
+    // Iterations beyond convergence or after a breakdown are harmless: CG
+    // with a fixed preconditioner keeps reducing the residual, and a step
+    // with non-positive curvature is not taken (alpha = 0).
+    double rr_prev = rr0;
+    int last_batch = 1;
     for (;;) {
         fetch_scalars(h);
         rr = h->host_sc[3];
@@ -340,15 +350,28 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
             break;
         }
         if (rr <= target_rr || it >= max_it) break;
-        if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, step_ba);
-        if (use_graph && gr.exec) {
-            cudaGraphLaunch(gr.exec, h->stream);
-            h->launches += gr.launches;
-            ++h->stats.graph_replays;
-        } else {
-            step_ba();
+        int batch = 1;
+        if (h->prm.cg_check == 0 && it >= 2 && rr < rr_prev) {
+            const double rate = std::pow(rr / rr_prev, 1.0 / last_batch);
+            if (rate < 1.0 && rate > 0.0) {
+                const double need = std::log(target_rr / rr) / std::log(rate);
+                batch = (int)std::fmin(8.0, std::fmax(1.0, std::floor(need)));
+            }
         }
-        ++it;
+        batch = std::min(batch, max_it - it);
+        rr_prev = rr;
+        last_batch = batch;
+        for (int b = 0; b < batch; ++b) {
+            if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, step_ba);
+            if (use_graph && gr.exec) {
+                cudaGraphLaunch(gr.exec, h->stream);
+                h->launches += gr.launches;
+                ++h->stats.graph_replays;
+            } else {
+                step_ba();
+            }
+            ++it;
+        }
     }
     if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;
     *rr_out = rr;

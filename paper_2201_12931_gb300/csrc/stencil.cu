@@ -271,7 +271,9 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 stv(o + c, r);
             }
             if constexpr (DOT) {
-                if constexpr (kDF) dotf += d32;   // FP32 per thread, FP64 across threads
+                // FP32 kernels: FP32 per thread (one column of a z chunk),
+                // FP64 across threads and CTAs, fixed order
+                if constexpr (kDF || std::is_same<T, float>::value) dotf += d32;
                 else dot += (double)d32;
             }
         }
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
         step(S3{}, P + 3);
     }
     if (DOT) {
-        double v = kDF ? (double)dotf : dot;
+        double v = (kDF || std::is_same<T, float>::value) ? (double)dotf : dot;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int w = tid >> 5, l = tid & 31;
         if (l == 0) sred[w] = v;

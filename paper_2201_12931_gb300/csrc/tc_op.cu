@@ -7,10 +7,11 @@
 // A (256 x 72): the element's 24 nodal values minus its corner-0 value (K0
 // annihilates the translation, which keeps FP32 cancellation out of the
 // product), split into TF32 pairs hi + lo and laid out as [hi | hi | lo].
+// (hi is the value rounded to TF32 with integer operations, lo = x - hi.)
 // B (32 x 72) holds [K0_hi | K0_lo | K0_hi] (rows 24..31 zero), so one
 // tcgen05.mma chain (M = 128 twice, N = 32, K = 72 in nine steps of 8)
 // accumulates hi K0_hi + hi K0_lo + lo K0_hi in FP32 in tensor memory: about
-// 22 significant bits of each product.  One thread issues the MMAs; every
+// 21 significant bits of each product.  One thread issues the MMAs; every
 // thread reads its element's row back with tcgen05.ld and scales it by the
 // modulus E_e.
 //
@@ -66,11 +67,9 @@ namespace {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
+// TF32 high part by integer rounding of the FP32 pattern (finite inputs):
+// round half away from zero to 10 stored mantissa bits
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 
 // shared-memory matrix descriptor: K-major, no swizzle (version 1)
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -311,11 +310,13 @@ __global__ void __launch_bounds__(kOpTX * kTcTY, 1)
                 uint32_t* const Arow = As + (tid >> 3) * kTcKB * 32 + (tid & 7) * 4;
 #pragma unroll
                 for (int kb = 0; kb < 6; ++kb) {
+                    // hi rounded to TF32; lo = x - hi is exact in FP32 and the
+                    // tensor core reads its top 11 bits (|lo| <= 2^-11 |x|)
                     uint32_t h[4], l[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        h[j] = tf32_rna(ue[4 * kb + j]);
-                        l[j] = tf32_rna(ue[4 * kb + j] - __uint_as_float(h[j]));
+                        h[j] = tf32_hi(ue[4 * kb + j]);
+                        l[j] = __float_as_uint(ue[4 * kb + j] - __uint_as_float(h[j]));
                     }
                     const uint4 hv = make_uint4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<uint4*>(Arow + kb * 32) = hv;

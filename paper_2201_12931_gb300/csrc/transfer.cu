@@ -18,78 +18,126 @@ inline unsigned grid_for(long long n, int threads) {
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Restriction r_c = diag(free_c) P^T diag(free_f) r_f.
+// Restriction marching along z: one thread per coarse (I, J) node column and
+// a chunk of coarse planes.  s_k = the masked in-plane 3 x 3 sum (weights
+// 1, 1/2) of fine plane k around (2I, 2J); r_c(K) = s_{2K-1}/2 + s_{2K} +
+// s_{2K+1}/2, and s_{2K+1} is reused as the lower plane of K + 1, so every
+// fine plane is summed once per coarse column.
 template <typename T>
-__global__ void k_restrict(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
-                           const T* __restrict__ rf, T* __restrict__ rc, int nxf, int nyf, int nzf) {
-    const int nxc = nxf / 2, nyc = nyf / 2, nzc = nzf / 2;
-    const int NXc = nxc + 1, NYc = nyc + 1, NZc = nzc + 1;
-    const int NXf = nxf + 1, NYf = nyf + 1, NZf = nzf + 1;
-    const long long nnc = (long long)NXc * NYc * NZc;
-    const long long N = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (N >= nnc) return;
-    const int I = (int)(N % NXc);
-    const long long t = N / NXc;
-    const int J = (int)(t % NYc), K = (int)(t / NYc);
-    T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int k = 2 * K + dz;
-        if (k < 0 || k >= NZf) continue;
-        const T wz = dz ? T(0.5) : T(1);
+__global__ void __launch_bounds__(256) k_restrict_z(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
+                                                    const T* __restrict__ rf, T* __restrict__ rc, int nxf, int nyf,
+                                                    int nzf, int czc) {
+    const int NXf = nxf + 1, NYf = nyf + 1;
+    const int NXc = nxf / 2 + 1, NYc = nyf / 2 + 1, NZc = nzf / 2 + 1;
+    const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
+    if (I >= NXc || J >= NYc) return;
+    const int K0 = blockIdx.z * czc, K1 = min(K0 + czc, NZc);
+    const long long fplane = (long long)NXf * NYf;
+    auto plane_sum = [&](int k, T* s) {
+        s[0] = s[1] = s[2] = T(0);
+        if (k < 0 || k > nzf) return;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const int j = 2 * J + dy;
             if (j < 0 || j >= NYf) continue;
-            const T wy = dy ? T(0.5) : T(1);
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 const int i = 2 * I + dx;
                 if (i < 0 || i >= NXf) continue;
-                const T w = wz * wy * (dx ? T(0.5) : T(1));
-                const long long n = i + (long long)NXf * (j + (long long)NYf * k);
+                const T w = (dx ? T(0.5) : T(1)) * (dy ? T(0.5) : T(1));
+                const long long n = i + (long long)NXf * j + fplane * k;
                 const unsigned mf = maskf[n];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    if (!((mf >> c) & 1u)) acc[c] += w * rf[3 * n + c];
+                    if (!((mf >> c) & 1u)) s[c] += w * rf[3 * n + c];
             }
         }
-    }
-    const unsigned mc = maskc[N];
+    };
+    T lo[3], mid[3], hi[3];
+    plane_sum(2 * K0 - 1, lo);
+    const long long ccol = I + (long long)NXc * J, cplane = (long long)NXc * NYc;
+    for (int K = K0; K < K1; ++K) {
+        plane_sum(2 * K, mid);
+        plane_sum(2 * K + 1, hi);
+        const long long N = ccol + cplane * K;
+        const unsigned mc = maskc[N];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rc[3 * N + c] = ((mc >> c) & 1u) ? T(0) : acc[c];
+        for (int c = 0; c < 3; ++c) {
+            rc[3 * N + c] = ((mc >> c) & 1u) ? T(0) : T(0.5) * lo[c] + mid[c] + T(0.5) * hi[c];
+            lo[c] = hi[c];
+        }
+    }
 }
 
-// T: arithmetic; TE / TU: storage of the coarse correction and the fine iterate
+constexpr int kRestrictCz = 8;
+
+// Prolongation u_f += diag(free_f) P diag(free_c) e_c, marching along z: one
+// thread per fine (i, j) node column and a chunk of fine planes.  The
+// in-plane interpolation of a coarse plane (up to four coarse nodes) is
+// formed once and serves the two fine planes around it, so a fine node costs
+// about two coarse gathers instead of up to eight, and no 64-bit index
+// division is needed.  T: arithmetic; TE / TU: storage of the coarse
+// correction and of the fine iterate.
 template <typename T, typename TE = T, typename TU = T>
-__global__ void k_prolong_add(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
-                              const TE* __restrict__ ec, TU* __restrict__ uf, int nxf, int nyf, int nzf) {
+__global__ void __launch_bounds__(256) k_prolong_z(const uint8_t* __restrict__ maskf, const uint8_t* __restrict__ maskc,
+                                                   const TE* __restrict__ ec, TU* __restrict__ uf, int nxf, int nyf,
+                                                   int nzf, int cz) {
     const int NXf = nxf + 1, NYf = nyf + 1, NZf = nzf + 1;
     const int NXc = nxf / 2 + 1, NYc = nyf / 2 + 1;
-    const long long nnf = (long long)NXf * NYf * NZf;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= nnf) return;
-    const int i = (int)(n % NXf);
-    const long long t = n / NXf;
-    const int j = (int)(t % NYf), k = (int)(t / NYf);
-    // per axis: one coarse node (even) or two with weight 1/2 (odd)
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
-    const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
-    T acc[3] = {T(0), T(0), T(0)};
-    for (int c2 = 0; c2 < nk; ++c2)
-        for (int b2 = 0; b2 < nj; ++b2)
-            for (int a2 = 0; a2 < ni; ++a2) {
-                const long long N = (I0 + a2) + (long long)NXc * ((J0 + b2) + (long long)NYc * (K0 + c2));
-                const unsigned mc = maskc[N];
-                const T w = wi * wj * wk;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    if (i >= NXf || j >= NYf) return;
+    const int k0 = blockIdx.z * cz, k1 = min(k0 + cz, NZf);
+    const bool two_x = i & 1, two_y = j & 1;
+    const int I0 = i >> 1, J0 = j >> 1;
+    const T w = (two_x ? T(0.5) : T(1)) * (two_y ? T(0.5) : T(1));
+    const long long ncp = (long long)NXc * NYc;
+    const long long c00 = I0 + (long long)NXc * J0;
+    auto coarse_plane = [&](int K, T* v) {
+        v[0] = v[1] = v[2] = T(0);
+        const long long b = (long long)K * ncp + c00;
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    if (!((mc >> c) & 1u)) acc[c] += w * (T)ec[3 * N + c];
+        for (int q = 0; q < 4; ++q) {
+            const int dx = q & 1, dy = q >> 1;
+            if ((dx && !two_x) || (dy && !two_y)) continue;
+            const long long N = b + dx + (long long)NXc * dy;
+            const unsigned mc = maskc[N];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (!((mc >> c) & 1u)) v[c] += w * (T)ec[3 * N + c];
+        }
+    };
+    T va[3], vb[3];
+    int Ka = -1;   // coarse plane whose interpolation is held in va
+    const long long col = i + (long long)NXf * j, fplane = (long long)NXf * NYf;
+    for (int k = k0; k < k1; ++k) {
+        const int K = k >> 1;
+        if (Ka != K) {
+            coarse_plane(K, va);
+            Ka = K;
+        }
+        T val[3] = {va[0], va[1], va[2]};
+        if (k & 1) {   // midway between coarse planes K and K + 1
+            coarse_plane(K + 1, vb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                val[c] = T(0.5) * (va[c] + vb[c]);
+                va[c] = vb[c];
             }
-    const unsigned mf = maskf[n];
+            Ka = K + 1;
+        }
+        const long long n = col + fplane * k;
+        const unsigned mf = maskf[n];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        if (!((mf >> c) & 1u)) uf[3 * n + c] = (TU)((T)uf[3 * n + c] + acc[c]);
+        for (int c = 0; c < 3; ++c)
+            if (!((mf >> c) & 1u)) uf[3 * n + c] = (TU)((T)uf[3 * n + c] + val[c]);
+    }
+}
+
+constexpr int kProlongCz = 16;
+
+inline dim3 prolong_grid(const Geom& gf) {
+    return dim3((gf.nx + 1 + 31) / 32, (gf.ny + 1 + 7) / 8, (gf.nz + 1 + kProlongCz - 1) / kProlongCz);
 }
 
 __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__ rc, int nxf, int nyf,
@@ -162,8 +210,8 @@ __global__ void k_masked_copy(long long nn, const uint8_t* __restrict__ mask, co
 template <typename T>
 void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* rf,
                        T* rc) {
-    const long long nnc = (long long)(gf.nx / 2 + 1) * (gf.ny / 2 + 1) * (gf.nz / 2 + 1);
-    k_restrict<T><<<grid_for(nnc, 256), 256, 0, c.s>>>(maskf, maskc, rf, rc, gf.nx, gf.ny, gf.nz);
+    const dim3 grid((gf.nx / 2 + 1 + 31) / 32, (gf.ny / 2 + 1 + 7) / 8, (gf.nz / 2 + 1 + kRestrictCz - 1) / kRestrictCz);
+    k_restrict_z<T><<<grid, dim3(32, 8), 0, c.s>>>(maskf, maskc, rf, rc, gf.nx, gf.ny, gf.nz, kRestrictCz);
     TOPO_LAUNCH_CHECK(c);
 }
 template void restrict_residual<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
@@ -173,7 +221,7 @@ template void restrict_residual<float>(const Ctx&, const Geom&, const uint8_t*, 
 
 template <typename T>
 void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* ec, T* uf) {
-    k_prolong_add<T><<<grid_for(gf.nn, 256), 256, 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz);
+    k_prolong_z<T><<<prolong_grid(gf), dim3(32, 8), 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz, kProlongCz);
     TOPO_LAUNCH_CHECK(c);
 }
 template void prolong_add<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
@@ -183,7 +231,8 @@ template void prolong_add<float>(const Ctx&, const Geom&, const uint8_t*, const 
 template <typename TE>
 void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const TE* ec,
                       bf16* uf) {
-    k_prolong_add<float, TE, bf16><<<grid_for(gf.nn, 256), 256, 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz);
+    k_prolong_z<float, TE, bf16><<<prolong_grid(gf), dim3(32, 8), 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz,
+                                                                        kProlongCz);
     TOPO_LAUNCH_CHECK(c);
 }
 template void prolong_add_bf16<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, bf16*);
