@@ -177,9 +177,11 @@ void free_all(topo_grid* h) {
     h->mkdf = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
-    if (h->graph64.exec) cudaGraphExecDestroy(h->graph64.exec);
-    if (h->graph32.exec) cudaGraphExecDestroy(h->graph32.exec);
-    h->graph64.exec = h->graph32.exec = nullptr;
+    for (int q = 0; q < 2; ++q) {
+        if (h->graph64[q].exec) cudaGraphExecDestroy(h->graph64[q].exec);
+        if (h->graph32[q].exec) cudaGraphExecDestroy(h->graph32[q].exec);
+        h->graph64[q].exec = h->graph32[q].exec = nullptr;
+    }
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->prof_ev.clear();
 }
@@ -946,7 +948,7 @@ topo_status topo_profile_enable(topo_handle h, int on) {
 topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
-    if (mode < 0 || mode > 3 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
+    if (mode < 0 || mode > 4 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
     CK(h, cudaStreamSynchronize(h->stream));
     for (int q = 0; q < 5; ++q) {
         launches[q] = 0;

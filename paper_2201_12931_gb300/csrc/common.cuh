@@ -139,7 +139,7 @@ struct topo_grid {
     double* host_sc = nullptr;      // pinned host mirror
     bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false, bf16_ready = false;
     long long launches = 0;
-    topo::PcgGraph graph64, graph32;   // captured PCG iterations per precision
+    topo::PcgGraph graph64[2], graph32[2];   // captured PCG iterations per precision and direction buffer
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
     topo_solve_stats stats{};
     std::string err;
@@ -152,7 +152,10 @@ constexpr int kRedBlocks = 1024;   // fixed grid of reduction kernels (determini
 constexpr int kProfMax = 65536;    // launch records of topo_profile_enable
 
 // ---- stencil.cu ----------------------------------------------------------
-enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3 };
+// ST_APPLY_P: K.p of CG with the direction update fused in: p = u + beta p_old
+// (u = z, f = p_old, beta from the device scalars or 0 when null), q = K p
+// written to out and p to pout
+enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3, ST_APPLY_P = 4 };
 // out = op(u, f); with dot != nullptr also writes per-CTA partial sums of
 //   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
 // and returns the number of partials written.
@@ -161,7 +164,8 @@ OpLaunch op_launch32(const Geom& g, int nsm);
 OpLaunch op_launch64(const Geom& g, int nsm);
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
-            const T* u, const T* f, T* out, T omega, double* dot_partials);
+            const T* u, const T* f, T* out, T omega, double* dot_partials, T* pout = nullptr,
+            const double* beta = nullptr);
 // V-cycle operators with BF16 iterates and FP32 arithmetic: u BF16, f FP32,
 // output BF16 (out_h) or FP32 (out_f).  Instantiated: JACOBI0 -> BF16,
 // JACOBI -> BF16, JACOBI -> FP32 (with or without dot), RESID -> FP32;

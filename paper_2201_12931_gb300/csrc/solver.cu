@@ -31,7 +31,7 @@ struct P<double> {
     static const double* WT(topo_grid* h) { return h->cs.WT64; }
     static double* y(topo_grid* h) { return h->cs.y64; }
     static const double* Ke(Level& l) { return l.Ke64; }
-    static PcgGraph& graph(topo_grid* h) { return h->graph64; }
+    static PcgGraph* graph(topo_grid* h) { return h->graph64; }
 };
 template <>
 struct P<float> {
@@ -43,11 +43,12 @@ struct P<float> {
     static const float* WT(topo_grid* h) { return h->cs.WT32; }
     static float* y(topo_grid* h) { return h->cs.y32; }
     static const float* Ke(Level& l) { return l.Ke32; }
-    static PcgGraph& graph(topo_grid* h) { return h->graph32; }
+    static PcgGraph* graph(topo_grid* h) { return h->graph32; }
 };
 
 template <typename T>
-int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot) {
+int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot, T* pout,
+             const double* beta) {
     Level& lv = h->lev[l];
     // FP32 operators with K.u on the tensor cores (the first sweep needs none)
     const bool tc = std::is_same<T, float>::value && h->prm.tensor_cores != 0 && mode != ST_JACOBI0;
@@ -79,7 +80,7 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
                             h->tcB, dot, h->tc_err);
     } else {
         np = stencil<T>(h->ctx(), mode, P<T>::op(lv), P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
-                        (T)h->prm.omega, dot);
+                        (T)h->prm.omega, dot, pout, beta);
     }
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
@@ -89,8 +90,10 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
     }
     return dot ? np : 0;
 }
-template int op_apply<double>(topo_grid*, int, int, const double*, const double*, double*, double*);
-template int op_apply<float>(topo_grid*, int, int, const float*, const float*, float*, double*);
+template int op_apply<double>(topo_grid*, int, int, const double*, const double*, double*, double*, double*,
+                              const double*);
+template int op_apply<float>(topo_grid*, int, int, const float*, const float*, float*, double*, float*,
+                             const double*);
 
 template <typename T>
 int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
@@ -301,19 +304,28 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
         return vcycle<T>(h, 0, r, z, vb.a, h->partials);
     };
     const bool flexible = std::is_same<T, float>::value && h->prm.precision == TOPO_MIXED_BF16;
+    // The direction update p = z + beta p is fused into the K.p kernel
+    // (ST_APPLY_P), which reads the old direction from one buffer and writes
+    // the new one to the other; the tensor-core operator has no fused form.
+    const bool fused = !(std::is_same<T, float>::value && h->prm.tensor_cores != 0);
+    T* pbuf[2] = {p, vb.b};   // vb.b of level 0 is free during the solve
     int np = precond();
     cg_beta(c, h->partials, np, h->sc);   // sets rz (beta unused on the first step)
-    cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
-    // K p, alpha, x += alpha p, r -= alpha q, r.r (on the stream current in h)
-    auto step_a = [&]() {
+    if (!fused) cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
+    // K p, alpha, x += alpha p, r -= alpha q, r.r (on the stream current in h);
+    // first: p = z; else p = z + beta p_old from pold into pnew
+    auto step_a = [&](bool first, T* pold, T* pnew) {
         const Ctx cc = h->ctx();
-        const int npa = op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
+        // (the first step reads z in place of p_old: beta is absent, nothing is added)
+        const int npa = fused ? op_apply<T>(h, ST_APPLY_P, 0, z, first ? z : pold, q, h->partials, pnew,
+                                            first ? nullptr : &h->sc->beta)
+                              : op_apply<T>(h, ST_APPLY, 0, pnew, nullptr, q, h->partials);
         cg_alpha(cc, h->partials, npa, h->sc);
-        cg_update_xr<T>(cc, n, h->sc, p, q, x, r, h->partials);
+        cg_update_xr<T>(cc, n, h->sc, pnew, q, x, r, h->partials);
         reduce_to(cc, h->partials, kRedBlocks, &h->sc->rr);
     };
-    // z = M^-1 r, beta, p = z + beta p, then the next step_a
-    auto step_ba = [&]() {
+    // z = M^-1 r, beta, p = z + beta p (pbuf[par] -> pbuf[par ^ 1]), then K p ...
+    auto step_ba = [&](int par) {
         const Ctx cc = h->ctx();
         const int npb = precond();
         cg_beta(cc, h->partials, npb, h->sc);
@@ -321,16 +333,21 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
             dot_partials<T, T>(cc, n, z, q, h->partials);
             cg_beta_flexible(cc, h->partials, kRedBlocks, h->sc);
         }
-        cg_update_p<T>(cc, n, h->sc, z, p);
-        step_a();
+        if (fused) {
+            step_a(false, pbuf[par], pbuf[par ^ 1]);
+        } else {
+            cg_update_p<T>(cc, n, h->sc, z, p);
+            step_a(false, p, p);
+        }
     };
-    // Every iteration after the first is the same sequence of launches on the
-    // same buffers (all scalars live on the device), so it is captured once
-    // into a CUDA graph and replayed; the host only reads r.r between
-    // replays.  Not while launches are being timed one by one.
-    PcgGraph& gr = P<T>::graph(h);
-    const bool use_graph = h->prm.graphs != 0 && !h->prof_on && !gr.failed;
-    step_a();
+    // Every iteration after the first is one of two fixed sequences of
+    // launches (the direction buffers alternate; all scalars live on the
+    // device), each captured once into a CUDA graph and replayed; the host
+    // only reads r.r between replays.  Not while launches are timed one by one.
+    PcgGraph* grs = P<T>::graph(h);
+    const bool use_graph = h->prm.graphs != 0 && !h->prof_on && !grs[0].failed && !grs[1].failed;
+    step_a(true, nullptr, fused ? pbuf[0] : p);
+    int cur = 0;   // pbuf[cur] holds the current direction
     int it = 1;
     // The host reads r.r (one stream synchronisation) after a batch of
     // iterations: one at a time for the first two, then as many as the
@@ -362,14 +379,17 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
         rr_prev = rr;
         last_batch = batch;
         for (int b = 0; b < batch; ++b) {
-            if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, step_ba);
+            const int par = fused ? cur : 0;
+            PcgGraph& gr = grs[par];
+            if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, [&]() { step_ba(par); });
             if (use_graph && gr.exec) {
                 cudaGraphLaunch(gr.exec, h->stream);
                 h->launches += gr.launches;
                 ++h->stats.graph_replays;
             } else {
-                step_ba();
+                step_ba(par);
             }
+            if (fused) cur ^= 1;
             ++it;
         }
     }

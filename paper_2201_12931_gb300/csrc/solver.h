@@ -5,7 +5,8 @@
 namespace topo {
 // returns the number of dot partials written (0 without dot)
 template <typename T>
-int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot);
+int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, double* dot, T* pout = nullptr,
+             const double* beta = nullptr);
 template <typename T>
 int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot);
 // V-cycle with BF16 iterates on levels 0 .. L-2 (FP32 arithmetic, FP32

@@ -40,11 +40,13 @@ template <typename T, typename TU, typename TO, int MODE, bool DOT>
 __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     k_op(const ModalK<T> mk, const typename OpStore<T>::type* __restrict__ E, const uint8_t* __restrict__ mask,
          const TU* __restrict__ u, const typename OpStore<T>::type* __restrict__ f, TO* __restrict__ out,
-         const int nx, const int ny, const int nz, const int cz, const T omega, double* __restrict__ partials) {
+         const int nx, const int ny, const int nz, const int cz, const T omega, double* __restrict__ partials,
+         TO* __restrict__ pout, const double* __restrict__ beta) {
     constexpr int TX = kOpTX, TY = op_ty<T>();
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
     constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
-    constexpr bool NEEDF = (MODE != ST_APPLY);
+    constexpr bool NEEDF = (MODE != ST_APPLY);   // ST_APPLY_P: p_old in the f slots
+    constexpr bool PUPD = (MODE == ST_APPLY_P);
     constexpr int nU = (TY + 1) * (TX + 1) * 4, nC = 3 * TY * TX * 4, nEs = TY * TX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double sred[32];
@@ -101,6 +103,8 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     TSl su[4][3], sf[4][3], sE[4];
     unsigned sm[4];
     TSl shv[2][3];
+    [[maybe_unused]] T shf[2][3] = {};        // halo p_old (ST_APPLY_P)
+    [[maybe_unused]] const T bet = (PUPD && beta) ? T(*beta) : T(0);
     unsigned shm[2];
     [[maybe_unused]] double srf[2][3];   // plane references (double-FP32)
 #pragma unroll
@@ -157,6 +161,11 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
             const TU* hb = u + 3 * pb + halo3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
+            if constexpr (PUPD) {
+                const typename OpStore<T>::type* hf = f + 3 * pb + halo3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) shf[S & 1][c] = okh ? (T)hf[c] : T(0);
+            }
         }
         sE[S] = (col_ok && P >= 1 && P <= nz) ? (TSl)E[(long long)(P - 1) * nx * ny + col_xy] : TSl(0);
     };
@@ -196,6 +205,15 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 st3(U + hoff, mu);
             }
         } else if (NEEDU) {
+            if constexpr (PUPD) {   // p = z + beta p_old (own and halo node)
+                if (beta) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        su[B][c] = su[B][c] + bet * sf[B][c];
+                        shv[B & 1][c] = shv[B & 1][c] + bet * shf[B & 1][c];
+                    }
+                }
+            }
             const unsigned cm = sm[B];
             T mu[3] = {su[B][0], su[B][1], su[B][2]};
             if (cm) {
@@ -255,9 +273,10 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                     uo = su[SO][c];
                 }
                 T r;
-                if constexpr (MODE == ST_APPLY) {
+                if constexpr (MODE == ST_APPLY || MODE == ST_APPLY_P) {
                     r = fixed ? uo : y[c];
                     if (DOT) d32 += to_acc(uo) * to_acc(r);
+                    if constexpr (PUPD) stv(pout + 3 * ((long long)Q * nplane) + own3 + c, uo);
                 } else if constexpr (MODE == ST_RESID) {
                     r = fo - (fixed ? uo : y[c]);
                     if (DOT) d32 += to_acc(r) * to_acc(r);
@@ -365,7 +384,8 @@ constexpr size_t op_smem_bytes() {
 
 template <typename T, int MODE, bool DOT, typename TU = T, typename TO = T>
 void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const typename OpStore<T>::type* E,
-               const uint8_t* mask, const TU* u, const typename OpStore<T>::type* f, TO* out, T omega, double* dot) {
+               const uint8_t* mask, const TU* u, const typename OpStore<T>::type* f, TO* out, T omega, double* dot,
+               TO* pout = nullptr, const double* beta = nullptr) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_op<T, TU, TO, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -373,15 +393,15 @@ void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const typen
         attr = true;
     }
     k_op<T, TU, TO, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, op_ty<T>()), op_smem_bytes<T>(), c.s>>>(
-        mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot);
+        mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot, pout, beta);
     TOPO_LAUNCH_CHECK(c);
 }
 
 template <typename T, int MODE>
 void launch_mode(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const T* u,
-                 const T* f, T* out, T omega, double* dot) {
-    if (dot) launch_op<T, MODE, true>(c, L, mk, E, mask, u, f, out, omega, dot);
-    else launch_op<T, MODE, false>(c, L, mk, E, mask, u, f, out, omega, nullptr);
+                 const T* f, T* out, T omega, double* dot, T* pout = nullptr, const double* beta = nullptr) {
+    if (dot) launch_op<T, MODE, true>(c, L, mk, E, mask, u, f, out, omega, dot, pout, beta);
+    else launch_op<T, MODE, false>(c, L, mk, E, mask, u, f, out, omega, nullptr, pout, beta);
 }
 
 // Dense assembly of the coarsest operator with identity Dirichlet rows.
@@ -538,8 +558,9 @@ OpLaunch op_launch64(const Geom& g, int nsm) { return op_launch(g, op_ty<double>
 
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
-            const T* u, const T* f, T* out, T omega, double* dot) {
+            const T* u, const T* f, T* out, T omega, double* dot, T* pout, const double* beta) {
     switch (mode) {
+        case ST_APPLY_P: launch_mode<T, ST_APPLY_P>(c, L, mk, E, mask, u, f, out, omega, dot, pout, beta); break;
         case ST_APPLY: launch_mode<T, ST_APPLY>(c, L, mk, E, mask, u, f, out, omega, dot); break;
         case ST_JACOBI: launch_mode<T, ST_JACOBI>(c, L, mk, E, mask, u, f, out, omega, dot); break;
         case ST_RESID: launch_mode<T, ST_RESID>(c, L, mk, E, mask, u, f, out, omega, dot); break;
@@ -548,9 +569,9 @@ int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, cons
     return L.gx * L.gy * L.gz;
 }
 template int stencil<double>(const Ctx&, int, const OpLaunch&, const ModalK<double>&, const double*, const uint8_t*,
-                             const double*, const double*, double*, double, double*);
+                             const double*, const double*, double*, double, double*, double*, const double*);
 template int stencil<float>(const Ctx&, int, const OpLaunch&, const ModalK<float>&, const float*, const uint8_t*,
-                            const float*, const float*, float*, float, double*);
+                            const float*, const float*, float*, float, double*, float*, const double*);
 
 int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
                  const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
