@@ -379,7 +379,7 @@ def peaks():
 
 
 OP_NAMES = {0: "K.u", 1: "Jacobi sweep", 2: "residual", 3: "first Jacobi sweep",
-            4: "K.p with p = z + beta p fused"}
+            4: "K.p with p = z + beta p fused", 5: "first two Jacobi sweeps fused"}
 PREC_NAMES = ("fp64", "fp32", "fp32, bf16 iterates", "double-fp32", "fp32, tensor-core element products")
 
 
@@ -391,17 +391,18 @@ def op_bytes(mode, prec, nn, ne):
         return 3 * nn * ({0: 8 + 8, 2: 8 + 8 + 4}[mode]) + ne * 8
     if prec == 2:   # BF16 iterates u (in) and u' (out, FP32 for the last sweep), FP32 f and residual
         su, sf, so = 2, 4, 2
-        return 3 * nn * ({0: su + so, 1: su + sf + so, 2: su + sf + 4, 3: sf + so, 4: 4 * 4}[mode]) + ne * 4
+        return 3 * nn * ({0: su + so, 1: su + sf + so, 2: su + sf + 4, 3: sf + so, 4: 4 * 4, 5: sf + so}[mode]) + ne * 4
     s = 8 if prec == 0 else 4   # prec 1 and 4: FP32 vectors
-    # K.u: u, y | Jacobi: u, f, u' | residual: u, f, r | first: f, u' | K.p fused: z, p_old, q, p
-    nvec = {0: 2, 1: 3, 2: 3, 3: 2, 4: 4}[mode]
+    # K.u: u, y | Jacobi: u, f, u' | residual: u, f, r | first: f, u' | K.p fused: z, p_old, q, p |
+    # first two sweeps: f, u''
+    nvec = {0: 2, 1: 3, 2: 3, 3: 2, 4: 4, 5: 2}[mode]
     return nvec * 3 * nn * s + ne * s
 
 
 def kernel_table(grid, nn, ne):
     peak, src = peaks()
     rows = []
-    for mode in range(5):
+    for mode in range(6):
         cnt, ms = grid.profile_read(mode)
         for prec in (0, 1, 2, 3, 4):
             if not cnt[prec]:

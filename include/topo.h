@@ -313,7 +313,8 @@ topo_status topo_profile_enable(topo_handle h, int on);
 
 /* Synchronises the stream and returns, for operator kind `mode` (0 = K.u,
  * 1 = Jacobi sweep, 2 = residual, 3 = first sweep from zero, 4 = K.p of CG
- * with the direction update p = z + beta p fused in), the number of
+ * with the direction update p = z + beta p fused in, 5 = the first two
+ * pre-smoothing sweeps from zero in one pass), the number of
  * recorded launches and their summed device time in milliseconds, split by
  * kernel precision: index 0 = FP64, 1 = FP32, 2 = FP32 arithmetic with BF16
  * iterates (V-cycle of TOPO_MIXED_BF16), 3 = double-FP32 (outer residual of

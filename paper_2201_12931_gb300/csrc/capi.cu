@@ -157,6 +157,7 @@ void free_all(topo_grid* h) {
     };
     for (auto& l : h->lev) {
         F(l.rho); F(l.E64); F(l.E32); F(l.mask);
+        F(l.Dinv64); F(l.Dinv32);
         F(l.v64.a); F(l.v64.b); F(l.v64.f);
         F(l.v32.a); F(l.v32.b); F(l.v32.f);
         F(l.ha); F(l.hb); F(l.Ke64); F(l.Ke32);
@@ -419,6 +420,8 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
         TRY(dalloc(h, &lv.E64, lv.g.ne));
         TRY(dalloc(h, &lv.E32, lv.g.ne));
         TRY(dalloc(h, &lv.mask, lv.g.nn));
+        TRY(dalloc(h, &lv.Dinv64, lv.g.nn));
+        TRY(dalloc(h, &lv.Dinv32, lv.g.nn));
     }
     const Geom& g0 = h->lev[0].g;
     const long long n0 = 3 * g0.nn;
@@ -522,6 +525,10 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
                 convert<double, float>(c, lc.g.ne, lc.E64, lc.E32);
             }
         }
+    }
+    for (int l = 0; l < h->L; ++l) {   // Jacobi diagonals from the final moduli of every level
+        Level& lv = h->lev[l];
+        diag_inverse(c, lv.g, lv.E64, h->mk64->kdiag, lv.Dinv64, lv.Dinv32);
     }
     if (h->prm.homogenize == 2) {
         for (int l = 1; l < h->L; ++l) {
@@ -948,7 +955,7 @@ topo_status topo_profile_enable(topo_handle h, int on) {
 topo_status topo_profile_read(topo_handle h, int mode, long long* launches, double* total_ms) {
     topo_status s = check_handle(h);
     if (s != TOPO_OK) return s;
-    if (mode < 0 || mode > 4 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
+    if (mode < 0 || mode > 5 || !launches || !total_ms) return fail(h, TOPO_BADARG, "bad arguments");
     CK(h, cudaStreamSynchronize(h->stream));
     for (int q = 0; q < 5; ++q) {
         launches[q] = 0;

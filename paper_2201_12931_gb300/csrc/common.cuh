@@ -64,6 +64,8 @@ struct Level {
     double* rho = nullptr;    // homogenized density
     double* E64 = nullptr;    // 2^l * (Emin + rho^p (E0 - Emin))
     float* E32 = nullptr;
+    double* Dinv64 = nullptr; // per node 1 / (kdiag * sum of E over the <= 8 elements around it)
+    float* Dinv32 = nullptr;
     uint8_t* mask = nullptr;
     VBuf<double> v64;
     VBuf<float> v32;
@@ -155,7 +157,10 @@ constexpr int kProfMax = 65536;    // launch records of topo_profile_enable
 // ST_APPLY_P: K.p of CG with the direction update fused in: p = u + beta p_old
 // (u = z, f = p_old, beta from the device scalars or 0 when null), q = K p
 // written to out and p to pout
-enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3, ST_APPLY_P = 4 };
+// ST_JACOBI2: the first two damped-Jacobi sweeps from u = 0 in one pass:
+// u1 = omega D^-1 f formed per node from f and D^-1, then u2 = u1 + omega
+// D^-1 (f - K u1) (u unused)
+enum StencilMode { ST_APPLY = 0, ST_JACOBI = 1, ST_RESID = 2, ST_JACOBI0 = 3, ST_APPLY_P = 4, ST_JACOBI2 = 5 };
 // out = op(u, f); with dot != nullptr also writes per-CTA partial sums of
 //   APPLY: u.out   JACOBI/JACOBI0: f.out   RESID: out.out
 // and returns the number of partials written.
@@ -164,7 +169,7 @@ OpLaunch op_launch32(const Geom& g, int nsm);
 OpLaunch op_launch64(const Geom& g, int nsm);
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
-            const T* u, const T* f, T* out, T omega, double* dot_partials, T* pout = nullptr,
+            const T* u, const T* f, T* out, T omega, double* dot_partials, const T* Dinv, T* pout = nullptr,
             const double* beta = nullptr);
 // V-cycle operators with BF16 iterates and FP32 arithmetic: u BF16, f FP32,
 // output BF16 (out_h) or FP32 (out_f).  Instantiated: JACOBI0 -> BF16,
@@ -172,7 +177,7 @@ int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, cons
 // returns -1 for any other combination, else as stencil().
 int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
                  const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
-                 double* dot_partials);
+                 double* dot_partials, const float* Dinv);
 // Operator in double-FP32 arithmetic (dfloat.cuh) on FP64 storage: u, f and
 // the modulus E are FP64, split into FP32 pairs on load; launch geometry of
 // the FP64 kernel.  Instantiated: APPLY -> FP64 out; RESID -> FP64 out; RESID
@@ -224,6 +229,8 @@ void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const 
                       bf16* uf);
 // coarse = scale * mean of the 8 children (densities: scale 1; moduli: scale 2)
 void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale);
+// per node D^-1 = 1 / (kdiag * sum of E over the <= 8 elements around it)
+void diag_inverse(const Ctx& c, const Geom& g, const double* E, double kdiag, double* Dinv64, float* Dinv32);
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0,
                  double Emin, double penal, double* E64, float* E32, int* bad_flag);
 void mask_from_dofs(const Ctx& c, long long nn, const uint8_t* fixed_dofs, uint8_t* mask);

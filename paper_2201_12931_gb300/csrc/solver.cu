@@ -26,6 +26,7 @@ struct P<double> {
     static const ModalK<double>& mk(topo_grid* h) { return *h->mk64; }
     static const OpLaunch& op(Level& l) { return l.op64; }
     static const double* E(Level& l) { return l.E64; }
+    static const double* Dinv(Level& l) { return l.Dinv64; }
     static VBuf<double>& vb(Level& l) { return l.v64; }
     static const double* W(topo_grid* h) { return h->cs.W64; }
     static const double* WT(topo_grid* h) { return h->cs.WT64; }
@@ -38,6 +39,7 @@ struct P<float> {
     static const ModalK<float>& mk(topo_grid* h) { return *h->mk32; }
     static const OpLaunch& op(Level& l) { return l.op32; }
     static const float* E(Level& l) { return l.E32; }
+    static const float* Dinv(Level& l) { return l.Dinv32; }
     static VBuf<float>& vb(Level& l) { return l.v32; }
     static const float* W(topo_grid* h) { return h->cs.W32; }
     static const float* WT(topo_grid* h) { return h->cs.WT32; }
@@ -51,7 +53,8 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
              const double* beta) {
     Level& lv = h->lev[l];
     // FP32 operators with K.u on the tensor cores (the first sweep needs none)
-    const bool tc = std::is_same<T, float>::value && h->prm.tensor_cores != 0 && mode != ST_JACOBI0;
+    const bool tc = std::is_same<T, float>::value && h->prm.tensor_cores != 0 &&
+                    (mode == ST_APPLY || mode == ST_JACOBI || mode == ST_RESID);
     const bool rec = h->prof_on && l == 0 && h->prof_n < kProfMax;
     if (rec) {
         if ((int)h->prof_ev.size() < 2 * (h->prof_n + 1)) {
@@ -80,7 +83,7 @@ int op_apply(topo_grid* h, int mode, int l, const T* u, const T* f, T* out, doub
                             h->tcB, dot, h->tc_err);
     } else {
         np = stencil<T>(h->ctx(), mode, P<T>::op(lv), P<T>::mk(h), P<T>::E(lv), lv.mask, u, f, out,
-                        (T)h->prm.omega, dot, pout, beta);
+                        (T)h->prm.omega, dot, P<T>::Dinv(lv), pout, beta);
     }
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
@@ -110,8 +113,15 @@ int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot) {
     T* oth = (cur == out) ? tmp : out;
     const long long n = 3 * lv.g.nn;
     if (pre > 0) {
-        op_apply<T>(h, ST_JACOBI0, l, nullptr, f, cur, nullptr);
-        for (int s = 1; s < pre; ++s) {
+        // the first two sweeps from zero as one kernel on matrix-free levels
+        const bool two = pre >= 2 && !(h->prm.homogenize == 2 && l > 0);
+        if (two) {
+            op_apply<T>(h, ST_JACOBI2, l, nullptr, f, oth, nullptr);
+            T* t = cur; cur = oth; oth = t;
+        } else {
+            op_apply<T>(h, ST_JACOBI0, l, nullptr, f, cur, nullptr);
+        }
+        for (int s = two ? 2 : 1; s < pre; ++s) {
             op_apply<T>(h, ST_JACOBI, l, cur, f, oth, nullptr);
             T* t = cur; cur = oth; oth = t;
         }
@@ -156,7 +166,7 @@ static int op_apply_bf16(topo_grid* h, int mode, int l, const bf16* u, const flo
         cudaEventRecord(h->prof_ev[2 * h->prof_n], h->stream);
     }
     const int np = stencil_bf16(h->ctx(), mode, lv.op32, *h->mk32, lv.E32, lv.mask, u, f, out_h, out_f,
-                                (float)h->prm.omega, dot);
+                                (float)h->prm.omega, dot, lv.Dinv32);
     if (rec) {
         cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], h->stream);
         h->prof_kind.resize(h->prof_n + 1);

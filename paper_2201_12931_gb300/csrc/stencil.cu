@@ -41,10 +41,11 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     k_op(const ModalK<T> mk, const typename OpStore<T>::type* __restrict__ E, const uint8_t* __restrict__ mask,
          const TU* __restrict__ u, const typename OpStore<T>::type* __restrict__ f, TO* __restrict__ out,
          const int nx, const int ny, const int nz, const int cz, const T omega, double* __restrict__ partials,
-         TO* __restrict__ pout, const double* __restrict__ beta) {
+         TO* __restrict__ pout, const double* __restrict__ beta, const typename OpStore<T>::type* __restrict__ Dinv) {
     constexpr int TX = kOpTX, TY = op_ty<T>();
     constexpr bool NEEDU = (MODE != ST_JACOBI0);
-    constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0);
+    constexpr bool NEEDD = (MODE == ST_JACOBI || MODE == ST_JACOBI0 || MODE == ST_JACOBI2);
+    constexpr bool J2 = (MODE == ST_JACOBI2);   // u1 = omega D^-1 f formed from f: u is not read
     constexpr bool NEEDF = (MODE != ST_APPLY);   // ST_APPLY_P: p_old in the f slots
     constexpr bool PUPD = (MODE == ST_APPLY_P);
     constexpr int nU = (TY + 1) * (TX + 1) * 4, nC = 3 * TY * TX * 4, nEs = TY * TX;
@@ -103,7 +104,9 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     TSl su[4][3], sf[4][3], sE[4];
     unsigned sm[4];
     TSl shv[2][3];
-    [[maybe_unused]] T shf[2][3] = {};        // halo p_old (ST_APPLY_P)
+    [[maybe_unused]] T shf[2][3] = {};        // halo p_old (ST_APPLY_P) or halo f (ST_JACOBI2)
+    [[maybe_unused]] T sdv[4] = {};           // own node D^-1 per plane slot (ST_JACOBI2)
+    [[maybe_unused]] T shd[2] = {};           // halo node D^-1 (ST_JACOBI2)
     [[maybe_unused]] const T bet = (PUPD && beta) ? T(*beta) : T(0);
     unsigned shm[2];
     [[maybe_unused]] double srf[2][3];   // plane references (double-FP32)
@@ -151,20 +154,24 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
             const typename OpStore<T>::type* fb_ = f + 3 * pb + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (NEEDU) su[S][c] = ok ? (T)ldv(ub + c) : T(0);
+                if (NEEDU && !J2) su[S][c] = ok ? (T)ldv(ub + c) : T(0);
                 if (NEEDF) sf[S][c] = ok ? (T)fb_[c] : T(0);
             }
+            if constexpr (J2) sdv[S] = ok ? (T)Dinv[pb + own_xy] : T(0);
         }
         if constexpr (NEEDU && !kDF) {
             const bool okh = pin && halo_ok;
             shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
             const TU* hb = u + 3 * pb + halo3;
+            if constexpr (!J2) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
-            if constexpr (PUPD) {
+                for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
+            }
+            if constexpr (PUPD || J2) {
                 const typename OpStore<T>::type* hf = f + 3 * pb + halo3;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) shf[S & 1][c] = okh ? (T)hf[c] : T(0);
+                if constexpr (J2) shd[S & 1] = okh ? (T)Dinv[pb + halo_xy] : T(0);
             }
         }
         sE[S] = (col_ok && P >= 1 && P <= nz) ? (TSl)E[(long long)(P - 1) * nx * ny + col_xy] : TSl(0);
@@ -205,6 +212,14 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 st3(U + hoff, mu);
             }
         } else if (NEEDU) {
+            if constexpr (J2) {   // first sweep from zero: u1 = omega D^-1 f (no scaling at fixed DOFs)
+                const unsigned cm1 = sm[B], chm1 = shm[B & 1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    su[B][c] = omega * sf[B][c] * (((cm1 >> c) & 1u) ? T(1) : sdv[B]);
+                    shv[B & 1][c] = omega * shf[B & 1][c] * (((chm1 >> c) & 1u) ? T(1) : shd[B & 1]);
+                }
+            }
             if constexpr (PUPD) {   // p = z + beta p_old (own and halo node)
                 if (beta) {
 #pragma unroll
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
             st3(Cb + nC / 3 + coff, st01);
             st3(Cb + 2 * (nC / 3) + coff, st11);
         }
-        if constexpr (NEEDD) Eb[ty * TX + tx] = stE;
+        if constexpr (NEEDD && !J2) Eb[ty * TX + tx] = stE;
         // start loading plane P + 1 (its slot held plane P - 3, no longer needed)
         if (P + 1 <= kz1) fetch(std::integral_constant<int, SN>{}, P + 1);
         if constexpr (kDF && NEEDF) {
@@ -254,8 +269,12 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
             }
+            // D^-1 of the output node: stored (first two sweeps) or formed
+            // from the column sums of E over the two layers around plane Q
             [[maybe_unused]] T rD = T(1);
-            if constexpr (NEEDD) {
+            if constexpr (J2) {
+                rD = sdv[SO];
+            } else if constexpr (NEEDD) {
                 const T* e = Eb + ty * TX + tx;
                 rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
@@ -280,7 +299,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 } else if constexpr (MODE == ST_RESID) {
                     r = fo - (fixed ? uo : y[c]);
                     if (DOT) d32 += to_acc(r) * to_acc(r);
-                } else if constexpr (MODE == ST_JACOBI) {
+                } else if constexpr (MODE == ST_JACOBI || MODE == ST_JACOBI2) {
                     r = fixed ? uo + omega * (fo - uo) : uo + omega * (fo - y[c]) * rD;
                     if (DOT) d32 += fo * r;
                 } else {
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                     st3(Cn + 2 * (nC / 3) + coff, st11);
                 }
             }
-            if constexpr (NEEDD) stE = sE[SL] + sE[B];
+            if constexpr (NEEDD && !J2) stE = sE[SL] + sE[B];
         } else if (NEEDU && P == kz0 - 1) {
             T c00[3], c10[3], c01[3], c11[3];
             ld3(U + uoff, c00);
@@ -385,7 +404,8 @@ constexpr size_t op_smem_bytes() {
 template <typename T, int MODE, bool DOT, typename TU = T, typename TO = T>
 void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const typename OpStore<T>::type* E,
                const uint8_t* mask, const TU* u, const typename OpStore<T>::type* f, TO* out, T omega, double* dot,
-               TO* pout = nullptr, const double* beta = nullptr) {
+               TO* pout = nullptr, const double* beta = nullptr,
+               const typename OpStore<T>::type* Dinv = nullptr) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_op<T, TU, TO, MODE, DOT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -393,15 +413,16 @@ void launch_op(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const typen
         attr = true;
     }
     k_op<T, TU, TO, MODE, DOT><<<dim3(L.gx, L.gy, L.gz), dim3(kOpTX, op_ty<T>()), op_smem_bytes<T>(), c.s>>>(
-        mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot, pout, beta);
+        mk, E, mask, u, f, out, L.g.nx, L.g.ny, L.g.nz, L.cz, omega, dot, pout, beta, Dinv);
     TOPO_LAUNCH_CHECK(c);
 }
 
 template <typename T, int MODE>
 void launch_mode(const Ctx& c, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask, const T* u,
-                 const T* f, T* out, T omega, double* dot, T* pout = nullptr, const double* beta = nullptr) {
-    if (dot) launch_op<T, MODE, true>(c, L, mk, E, mask, u, f, out, omega, dot, pout, beta);
-    else launch_op<T, MODE, false>(c, L, mk, E, mask, u, f, out, omega, nullptr, pout, beta);
+                 const T* f, T* out, T omega, double* dot, const T* Dinv, T* pout = nullptr,
+                 const double* beta = nullptr) {
+    if (dot) launch_op<T, MODE, true>(c, L, mk, E, mask, u, f, out, omega, dot, pout, beta, Dinv);
+    else launch_op<T, MODE, false>(c, L, mk, E, mask, u, f, out, omega, nullptr, pout, beta, Dinv);
 }
 
 // Dense assembly of the coarsest operator with identity Dirichlet rows.
@@ -558,33 +579,39 @@ OpLaunch op_launch64(const Geom& g, int nsm) { return op_launch(g, op_ty<double>
 
 template <typename T>
 int stencil(const Ctx& c, int mode, const OpLaunch& L, const ModalK<T>& mk, const T* E, const uint8_t* mask,
-            const T* u, const T* f, T* out, T omega, double* dot, T* pout, const double* beta) {
+            const T* u, const T* f, T* out, T omega, double* dot, const T* Dinv, T* pout, const double* beta) {
     switch (mode) {
-        case ST_APPLY_P: launch_mode<T, ST_APPLY_P>(c, L, mk, E, mask, u, f, out, omega, dot, pout, beta); break;
-        case ST_APPLY: launch_mode<T, ST_APPLY>(c, L, mk, E, mask, u, f, out, omega, dot); break;
-        case ST_JACOBI: launch_mode<T, ST_JACOBI>(c, L, mk, E, mask, u, f, out, omega, dot); break;
-        case ST_RESID: launch_mode<T, ST_RESID>(c, L, mk, E, mask, u, f, out, omega, dot); break;
-        default: launch_mode<T, ST_JACOBI0>(c, L, mk, E, mask, u, f, out, omega, dot); break;
+        case ST_APPLY_P:
+            launch_mode<T, ST_APPLY_P>(c, L, mk, E, mask, u, f, out, omega, dot, Dinv, pout, beta);
+            break;
+        case ST_APPLY: launch_mode<T, ST_APPLY>(c, L, mk, E, mask, u, f, out, omega, dot, Dinv); break;
+        case ST_JACOBI: launch_mode<T, ST_JACOBI>(c, L, mk, E, mask, u, f, out, omega, dot, Dinv); break;
+        case ST_RESID: launch_mode<T, ST_RESID>(c, L, mk, E, mask, u, f, out, omega, dot, Dinv); break;
+        case ST_JACOBI2:   // pre-smoothing only: no dot
+            launch_op<T, ST_JACOBI2, false, T, T>(c, L, mk, E, mask, u, f, out, omega, nullptr, nullptr, nullptr, Dinv);
+            return 0;
+        default: launch_mode<T, ST_JACOBI0>(c, L, mk, E, mask, u, f, out, omega, dot, Dinv); break;
     }
     return L.gx * L.gy * L.gz;
 }
 template int stencil<double>(const Ctx&, int, const OpLaunch&, const ModalK<double>&, const double*, const uint8_t*,
-                             const double*, const double*, double*, double, double*, double*, const double*);
+                             const double*, const double*, double*, double, double*, const double*, double*,
+                             const double*);
 template int stencil<float>(const Ctx&, int, const OpLaunch&, const ModalK<float>&, const float*, const uint8_t*,
-                            const float*, const float*, float*, float, double*, float*, const double*);
+                            const float*, const float*, float*, float, double*, const float*, float*, const double*);
 
 int stencil_bf16(const Ctx& c, int mode, const OpLaunch& L, const ModalK<float>& mk, const float* E,
                  const uint8_t* mask, const bf16* u, const float* f, bf16* out_h, float* out_f, float omega,
-                 double* dot) {
+                 double* dot, const float* Dinv) {
     if (mode == ST_JACOBI0 && out_h && !dot) {
-        launch_op<float, ST_JACOBI0, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr);
+        launch_op<float, ST_JACOBI0, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr, nullptr, nullptr, Dinv);
     } else if (mode == ST_JACOBI && out_h && !dot) {
-        launch_op<float, ST_JACOBI, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr);
+        launch_op<float, ST_JACOBI, false, bf16, bf16>(c, L, mk, E, mask, u, f, out_h, omega, nullptr, nullptr, nullptr, Dinv);
     } else if (mode == ST_JACOBI && out_f) {
-        if (dot) launch_op<float, ST_JACOBI, true, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, dot);
-        else launch_op<float, ST_JACOBI, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
+        if (dot) launch_op<float, ST_JACOBI, true, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, dot, nullptr, nullptr, Dinv);
+        else launch_op<float, ST_JACOBI, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr, nullptr, nullptr, Dinv);
     } else if (mode == ST_RESID && out_f && !dot) {
-        launch_op<float, ST_RESID, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr);
+        launch_op<float, ST_RESID, false, bf16, float>(c, L, mk, E, mask, u, f, out_f, omega, nullptr, nullptr, nullptr, Dinv);
     } else {
         return -1;   // combination not instantiated
     }

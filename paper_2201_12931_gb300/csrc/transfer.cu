@@ -168,6 +168,28 @@ __device__ __forceinline__ double rpow(double r, double p, int ip) {
     return pow(r, p);
 }
 
+// D^-1 of the Jacobi sweeps: node (i, j, k) sums E over the in-grid elements
+// (i-1..i, j-1..j, k-1..k) in a fixed order (E carries the level scale 2^l)
+__global__ void k_diag_inv(const double* __restrict__ E, int nx, int ny, int nz, double kdiag,
+                           double* __restrict__ D64, float* __restrict__ D32) {
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const long long nn = (long long)NX * NY * NZ;
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const int i = (int)(n % NX);
+    const long long t = n / NX;
+    const int j = (int)(t % NY), k = (int)(t / NY);
+    double s = 0.0;
+    for (int ez = k - 1; ez <= k; ++ez)
+        for (int ey = j - 1; ey <= j; ++ey)
+            for (int ex = i - 1; ex <= i; ++ex)
+                if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
+                    s += E[ex + (long long)nx * (ey + (long long)ny * ez)];
+    const double d = s > 0.0 ? 1.0 / (kdiag * s) : 0.0;
+    D64[n] = d;
+    D32[n] = (float)d;
+}
+
 __global__ void k_simp(long long ne, const double* __restrict__ rho, double scale, double E0, double Emin,
                        double penal, int ipenal, double* __restrict__ E64, float* __restrict__ E32, int* bad) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -241,6 +263,11 @@ template void prolong_add_bf16<bf16>(const Ctx&, const Geom&, const uint8_t*, co
 void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale) {
     const long long nec = (long long)(gf.nx / 2) * (gf.ny / 2) * (gf.nz / 2);
     k_homogenize<<<grid_for(nec, 256), 256, 0, c.s>>>(rho_f, rho_c, gf.nx, gf.ny, gf.nz, scale);
+    TOPO_LAUNCH_CHECK(c);
+}
+
+void diag_inverse(const Ctx& c, const Geom& g, const double* E, double kdiag, double* Dinv64, float* Dinv32) {
+    k_diag_inv<<<grid_for(g.nn, 256), 256, 0, c.s>>>(E, g.nx, g.ny, g.nz, kdiag, Dinv64, Dinv32);
     TOPO_LAUNCH_CHECK(c);
 }
 
