@@ -551,9 +551,13 @@ OpLaunch op_launch(const Geom& g, int ty, int target_ctas, int resident_ctas) {
     const long long xy = (long long)L.gx * L.gy;
     const int NZ = g.nz + 1;
     const long long gz_min = (target_ctas + xy - 1) / xy;
+    // chunks of at least 4 planes (each chunk re-reads 3 planes): small
+    // levels get many short chunks, as their launches are bound by the
+    // latency of the march, not by memory
+    constexpr int kMinCz = 4;
     auto chunk = [&](long long gz) {
         int cz = (int)((NZ + gz - 1) / gz);
-        return cz < 16 ? (NZ < 16 ? NZ : 16) : cz;
+        return cz < kMinCz ? (NZ < kMinCz ? NZ : kMinCz) : cz;
     };
     int best_cz = chunk(gz_min);
     double best_cost = -1.0;
@@ -566,7 +570,7 @@ OpLaunch op_launch(const Geom& g, int ty, int target_ctas, int resident_ctas) {
             best_cost = cost;
             best_cz = cz;
         }
-        if (cz <= 16) break;   // chunks cannot get shorter
+        if (cz <= kMinCz) break;   // chunks cannot get shorter
     }
     L.cz = best_cz;
     L.gz = (NZ + best_cz - 1) / best_cz;

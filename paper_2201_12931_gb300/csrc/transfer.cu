@@ -136,8 +136,24 @@ __global__ void __launch_bounds__(256) k_prolong_z(const uint8_t* __restrict__ m
 
 constexpr int kProlongCz = 16;
 
+// z chunk of a transfer kernel with `columns` (i, j) threads over `planes`
+// planes: as long as cz_max (plane sums reused along the march) while the
+// grid still fills a GB300 (152 SMs x 2048 threads), shorter on small levels,
+// whose launches are bound by the latency of the march, not by memory
+inline int transfer_cz(long long columns, int planes, int cz_max) {
+    constexpr long long kFull = 152LL * 2048;
+    const long long chunks = (kFull + columns - 1) / columns;
+    const long long cz = (planes + chunks - 1) / chunks;
+    return (int)(cz < 1 ? 1 : (cz > cz_max ? cz_max : cz));
+}
+
+inline int prolong_cz(const Geom& gf) {
+    return transfer_cz((long long)(gf.nx + 1) * (gf.ny + 1), gf.nz + 1, kProlongCz);
+}
+
 inline dim3 prolong_grid(const Geom& gf) {
-    return dim3((gf.nx + 1 + 31) / 32, (gf.ny + 1 + 7) / 8, (gf.nz + 1 + kProlongCz - 1) / kProlongCz);
+    const int cz = prolong_cz(gf);
+    return dim3((gf.nx + 1 + 31) / 32, (gf.ny + 1 + 7) / 8, (gf.nz + 1 + cz - 1) / cz);
 }
 
 __global__ void k_homogenize(const double* __restrict__ rf, double* __restrict__ rc, int nxf, int nyf,
@@ -232,8 +248,9 @@ __global__ void k_masked_copy(long long nn, const uint8_t* __restrict__ mask, co
 template <typename T>
 void restrict_residual(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* rf,
                        T* rc) {
-    const dim3 grid((gf.nx / 2 + 1 + 31) / 32, (gf.ny / 2 + 1 + 7) / 8, (gf.nz / 2 + 1 + kRestrictCz - 1) / kRestrictCz);
-    k_restrict_z<T><<<grid, dim3(32, 8), 0, c.s>>>(maskf, maskc, rf, rc, gf.nx, gf.ny, gf.nz, kRestrictCz);
+    const int czc = transfer_cz((long long)(gf.nx / 2 + 1) * (gf.ny / 2 + 1), gf.nz / 2 + 1, kRestrictCz);
+    const dim3 grid((gf.nx / 2 + 1 + 31) / 32, (gf.ny / 2 + 1 + 7) / 8, (gf.nz / 2 + 1 + czc - 1) / czc);
+    k_restrict_z<T><<<grid, dim3(32, 8), 0, c.s>>>(maskf, maskc, rf, rc, gf.nx, gf.ny, gf.nz, czc);
     TOPO_LAUNCH_CHECK(c);
 }
 template void restrict_residual<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
@@ -243,7 +260,7 @@ template void restrict_residual<float>(const Ctx&, const Geom&, const uint8_t*, 
 
 template <typename T>
 void prolong_add(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const T* ec, T* uf) {
-    k_prolong_z<T><<<prolong_grid(gf), dim3(32, 8), 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz, kProlongCz);
+    k_prolong_z<T><<<prolong_grid(gf), dim3(32, 8), 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz, prolong_cz(gf));
     TOPO_LAUNCH_CHECK(c);
 }
 template void prolong_add<double>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const double*,
@@ -254,7 +271,7 @@ template <typename TE>
 void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const uint8_t* maskc, const TE* ec,
                       bf16* uf) {
     k_prolong_z<float, TE, bf16><<<prolong_grid(gf), dim3(32, 8), 0, c.s>>>(maskf, maskc, ec, uf, gf.nx, gf.ny, gf.nz,
-                                                                        kProlongCz);
+                                                                        prolong_cz(gf));
     TOPO_LAUNCH_CHECK(c);
 }
 template void prolong_add_bf16<float>(const Ctx&, const Geom&, const uint8_t*, const uint8_t*, const float*, bf16*);
