@@ -165,6 +165,22 @@ topo_status topo_solve_state(topo_handle h, double rel_tol, int max_it,
  * C_out (host) may be NULL; dc_dev_out (device, nx*ny*nz FP64) may be NULL. */
 topo_status topo_compliance_and_sensitivity(topo_handle h, double* C_out, double* dc_dev_out);
 
+/* One state step from host memory (Sec. 4.2: the solver is called from the
+ * host program with its own arrays, as the paper's mex interface is): copies
+ * the physical density rho_host (host, nx*ny*nz FP64, x fastest; pinned for
+ * an asynchronous copy, pageable works) to the device as topo_set_density
+ * does, solves as topo_solve_state (from the handle's current solution:
+ * topo_reset_solution first for a solve from zero), forms C and dc as
+ * topo_compliance_and_sensitivity and copies dc to dc_host_out (host,
+ * nx*ny*nz FP64; NULL = not copied).  C_out, iters_out, relres_out: host,
+ * may be NULL.  Synchronises the handle's stream before returning; uses a
+ * handle-owned device buffer for dc (no allocation per call).  Returns the
+ * solve's status (TOPO_MAXITER / TOPO_BREAKDOWN with C and dc of the
+ * returned iterate, as topo_solve_state describes), or TOPO_BADARG (NULL
+ * rho, boundary conditions not set, density outside [0, 1]) / TOPO_CUDA. */
+topo_status topo_state_step_host(topo_handle h, const double* rho_host, double rel_tol, int max_it,
+                                 double* C_out, double* dc_host_out, int* iters_out, double* relres_out);
+
 /* Density filter with the weights of Eqs. Neighbourhood / NB_dist
  * (w = r - |x_i - x_e| for element-centre distances below r, cut at the
  * domain boundary and normalised by the in-domain weight sum S_e):

@@ -42,6 +42,8 @@ _SIGS = {
     "topo_set_bc_loads": ([H, P, P], C.c_int),
     "topo_solve_state": ([H, C.c_double, C.c_int, P, C.POINTER(C.c_int), C.POINTER(C.c_double)], C.c_int),
     "topo_compliance_and_sensitivity": ([H, C.POINTER(C.c_double), P], C.c_int),
+    "topo_state_step_host": ([H, P, C.c_double, C.c_int, C.POINTER(C.c_double), P, C.POINTER(C.c_int),
+                              C.POINTER(C.c_double)], C.c_int),
     "topo_filter": ([H, C.c_double, P, P, C.c_int], C.c_int),
     "topo_oc_update": ([H, C.c_double, C.c_double, C.c_double, P, P, C.POINTER(C.c_double)], C.c_int),
     "topo_sensitivity_filter": ([H, C.c_double, C.c_double, P, P, P], C.c_int),

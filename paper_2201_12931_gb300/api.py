@@ -137,6 +137,29 @@ class TopoGrid:
         self._check(self.lib.topo_compliance_and_sensitivity(self._h, C.byref(Cv), dp))
         return Cv.value, dc
 
+    def state_step_host(self, rho: torch.Tensor, rel_tol=1e-8, max_it=1000, dc: torch.Tensor | None = None,
+                        allow_breakdown=False):
+        """topo_state_step_host: density from host memory, solve, C, and dc
+        into a host tensor.  rho and dc are CPU float64 tensors (pinned for
+        asynchronous copies).  Returns (C, dc, SolveResult)."""
+        for name, v in (("rho", rho), ("dc", dc)):
+            if v is None:
+                continue
+            if not isinstance(v, torch.Tensor) or v.is_cuda or v.dtype != torch.float64 or not v.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous CPU float64 tensor")
+            if v.numel() != self.ne:
+                raise ValueError(f"{name} must have {self.ne} elements, got {v.numel()}")
+        Cv = C.c_double(0.0)
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        st = self.lib.topo_state_step_host(self._h, C.c_void_p(rho.data_ptr()), float(rel_tol), int(max_it),
+                                           C.byref(Cv), C.c_void_p(dc.data_ptr()) if dc is not None else None,
+                                           C.byref(it), C.byref(rr))
+        self._check(st, allow=(L.TOPO_MAXITER,) + ((L.TOPO_BREAKDOWN,) if allow_breakdown else ()))
+        self.generation += 1
+        s = self.stats()
+        return Cv.value, dc, SolveResult(st, it.value, rr.value, s.outer_steps, s.solve_ms, s.graph_replays)
+
     def filter(self, r: float, x: torch.Tensor, transpose=False, out: torch.Tensor | None = None):
         out = torch.empty_like(x) if out is None else out
         self._check(self.lib.topo_filter(self._h, float(r), _ptr(x, torch.float64, self.ne, "in"),

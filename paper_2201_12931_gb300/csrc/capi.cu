@@ -487,13 +487,12 @@ topo_status topo_destroy_grid(topo_handle h) {
 
 const char* topo_last_error(topo_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
-topo_status topo_set_density(topo_handle h, const double* rho_dev) {
-    topo_status s = check_handle(h);
-    if (s != TOPO_OK) return s;
-    if (!rho_dev) return fail(h, TOPO_BADARG, "rho is NULL");
+// the density from device (kind = DeviceToDevice) or host memory
+// (HostToDevice) into the level-0 copy, then moduli and coarse levels
+static topo_status set_density_from(topo_handle h, const double* rho, cudaMemcpyKind kind) {
     const Ctx c = h->ctx();
     CK(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
-    CK(h, cudaMemcpyAsync(h->lev[0].rho, rho_dev, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->lev[0].rho, rho, sizeof(double) * h->lev[0].g.ne, kind, h->stream));
     if (h->prm.homogenize == 2 && h->L > 1) {   // stored Galerkin element matrices of levels 1 .. L-1
         galerkin_init_constants();
         if (!h->G64) {
@@ -542,6 +541,13 @@ topo_status topo_set_density(topo_handle h, const double* rho_dev) {
     h->have_density = true;
     h->coarse_dirty = true;
     return TOPO_OK;
+}
+
+topo_status topo_set_density(topo_handle h, const double* rho_dev) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_dev) return fail(h, TOPO_BADARG, "rho is NULL");
+    return set_density_from(h, rho_dev, cudaMemcpyDeviceToDevice);
 }
 
 topo_status topo_set_bc_loads(topo_handle h, const uint8_t* fixed_dev, const double* f_dev) {
@@ -652,6 +658,27 @@ topo_status topo_compliance_and_sensitivity(topo_handle h, double* C_out, double
     }
     CK(h, cudaGetLastError());
     return TOPO_OK;
+}
+
+topo_status topo_state_step_host(topo_handle h, const double* rho_host, double rel_tol, int max_it, double* C_out,
+                                 double* dc_host_out, int* iters_out, double* relres_out) {
+    topo_status s = check_handle(h);
+    if (s != TOPO_OK) return s;
+    if (!rho_host) return fail(h, TOPO_BADARG, "rho is NULL");
+    s = set_density_from(h, rho_host, cudaMemcpyHostToDevice);
+    if (s != TOPO_OK) return s;
+    const topo_status st = topo_solve_state(h, rel_tol, max_it, nullptr, iters_out, relres_out);
+    if (st != TOPO_OK && st != TOPO_MAXITER && st != TOPO_BREAKDOWN) return st;
+    const std::string msg = h->err;   // the solve's message survives the steps below
+    s = topo_compliance_and_sensitivity(h, C_out, dc_host_out ? h->dc_work : nullptr);
+    if (s != TOPO_OK) return s;
+    if (dc_host_out) {
+        CK(h, cudaMemcpyAsync(dc_host_out, h->dc_work, sizeof(double) * h->lev[0].g.ne, cudaMemcpyDeviceToHost,
+                              h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    h->err = msg;
+    return st;
 }
 
 topo_status topo_filter(topo_handle h, double r, const double* in_dev, double* out_dev, int transpose) {

@@ -97,6 +97,7 @@ def test_null_handle_calls_are_rejected(lib):
     assert lib.topo_gravity_load(None, 0.1, None, None, None) == 1
     assert lib.topo_gravity_sensitivity(None, 0.1, None) == 1
     assert lib.topo_compliance_and_sensitivity(None, None, None) == 1
+    assert lib.topo_state_step_host(None, None, 1e-8, 10, None, None, None, None) == 1
     assert lib.topo_vcycle(None, 0, None, None) == 1
 
 
