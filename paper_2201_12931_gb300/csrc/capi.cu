@@ -357,8 +357,9 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     if (p.cg_check < 0 || p.cg_check > 1) return fail(nullptr, TOPO_BADARG, "cg_check must be 0 or 1");
     if (p.homogenize == 2 && p.precision == TOPO_MIXED_BF16)
         return fail(nullptr, TOPO_BADARG, "homogenize = 2 (stored Galerkin operators) is not combined with BF16 iterates");
-    if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 > (1LL << 40))
-        return fail(nullptr, TOPO_BADARG, "grid too large");
+    // the operator kernels index the nodal vectors with 32-bit integers
+    if ((long long)(nx + 1) * (ny + 1) * (nz + 1) * 3 >= (1LL << 31))
+        return fail(nullptr, TOPO_BADARG, "grid too large: 3 * nodes must be below 2^31");
 
     topo_grid* h = new (std::nothrow) topo_grid();
     if (!h) return fail(nullptr, TOPO_OOM, "host allocation failed");

@@ -63,7 +63,13 @@ struct DotAcc<dfl> {
 __device__ __forceinline__ float to_acc(dfl v) { return df_to_float(v); }
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ double to_acc(double v) { return v; }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// Jacobi diagonal inverse: the hardware approximate reciprocal (rcp.approx,
+// about 1 ulp); any fixed diagonal keeps the smoother symmetric
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 }  // namespace topo

@@ -75,11 +75,16 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     const bool col_ok = in >= 0 && in < nx && jn >= 0 && jn < ny;
     const bool out_ok = tx >= 1 && ty >= 1 && node_ok;
     const bool has_halo = tid < TY + 1 + TX;
+    [[maybe_unused]] const bool halo_warp = (tid >> 5) <= ((TY + TX) >> 5);   // warp holds halo threads
     const int hsx = tid < TY + 1 ? TX : tid - TY - 1;
     const int hsy = tid < TY + 1 ? tid : TY;
     const int hx = i0 - 1 + hsx, hy = j0 - 1 + hsy;
     const bool halo_ok = has_halo && hx >= 0 && hx < NX && hy >= 0 && hy < NY;
-    const long long nplane = (long long)NX * NY;
+    // 32-bit vector indices (topo_create_grid keeps 3 * nodes below 2^31):
+    // fewer address instructions; the fused K.p keeps 64-bit indices, with
+    // which it needs fewer registers (measured: 32-bit spilled and was slower)
+    using Ix = std::conditional_t<PUPD, long long, int>;
+    const Ix nplane = (Ix)NX * NY;
     const int own_xy = node_ok ? in + NX * jn : 0;
     const int halo_xy = halo_ok ? hx + NX * hy : 0;
     const int col_xy = col_ok ? in + nx * jn : 0;
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
     auto fetch = [&](auto Sc, int P) {
         constexpr int S = decltype(Sc)::value;
         const bool pin = P >= 0 && P <= nz;
-        const long long pb = (long long)P * nplane;
+        const Ix pb = (Ix)P * nplane;
         if constexpr (kDF) {
             // raw FP64 words: own and halo node, the plane's reference (tile
             // corner node); f is loaded by the step (one plane behind)
@@ -159,10 +164,14 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
             }
             if constexpr (J2) sdv[S] = ok ? (T)Dinv[pb + own_xy] : T(0);
         }
-        if constexpr (NEEDU && !kDF) {
+        // residual and K.u: the halo loads behind a warp-uniform branch (two of
+        // the eight warps hold halo threads); measured faster there, slower in
+        // the Jacobi and fused modes
+        [[maybe_unused]] constexpr bool kHaloBranch = (MODE == ST_RESID || MODE == ST_APPLY);
+        if constexpr (NEEDU && !kDF) if (!kHaloBranch || halo_warp) {
             const bool okh = pin && halo_ok;
             shm[S & 1] = okh ? mask[pb + halo_xy] : 0u;
-            const TU* hb = u + 3 * pb + halo3;
+            [[maybe_unused]] const TU* hb = u + 3 * pb + halo3;
             if constexpr (!J2) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) shv[S & 1][c] = okh ? (T)ldv(hb + c) : T(0);
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 if constexpr (J2) shd[S & 1] = okh ? (T)Dinv[pb + halo_xy] : T(0);
             }
         }
-        sE[S] = (col_ok && P >= 1 && P <= nz) ? (TSl)E[(long long)(P - 1) * nx * ny + col_xy] : TSl(0);
+        sE[S] = (col_ok && P >= 1 && P <= nz) ? (TSl)E[(Ix)(P - 1) * nx * ny + col_xy] : TSl(0);
     };
 
     // step of node plane P, B = P & 3 (static)
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
         if constexpr (kDF && NEEDF) {
             // f of plane P - 1, output by the next step (slot SL is not read here)
             const bool okf = P - 1 >= 0 && P - 1 <= nz && node_ok;
-            const double* ff = f + 3 * ((long long)(P - 1) * nplane) + own3;
+            const double* ff = f + 3 * ((Ix)(P - 1) * nplane) + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) sf[SL][c] = okf ? ff[c] : 0.0;
         }
@@ -278,7 +287,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 const T* e = Eb + ty * TX + tx;
                 rD = recip(mk.kdiag * (e[0] + e[-1] + e[-TX] + e[-TX - 1]));
             }
-            TO* o = out + 3 * ((long long)Q * nplane) + own3;
+            TO* o = out + 3 * ((Ix)Q * nplane) + own3;
             const unsigned m2 = sm[SO];
             typename DotAcc<T>::type d32 = 0;
 #pragma unroll
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 [[maybe_unused]] T uo;
                 [[maybe_unused]] const T fo = T(sf[SO][c]);
                 if constexpr (kDF) {   // fixed rows read u itself (the slots are not kept)
-                    uo = fixed ? T((double)u[3 * ((long long)Q * nplane) + own3 + c]) : T(0);
+                    uo = fixed ? T((double)u[3 * ((Ix)Q * nplane) + own3 + c]) : T(0);
                 } else {
                     uo = su[SO][c];
                 }
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 if constexpr (MODE == ST_APPLY || MODE == ST_APPLY_P) {
                     r = fixed ? uo : y[c];
                     if (DOT) d32 += to_acc(uo) * to_acc(r);
-                    if constexpr (PUPD) stv(pout + 3 * ((long long)Q * nplane) + own3 + c, uo);
+                    if constexpr (PUPD) stv(pout + 3 * ((Ix)Q * nplane) + own3 + c, uo);
                 } else if constexpr (MODE == ST_RESID) {
                     r = fo - (fixed ? uo : y[c]);
                     if (DOT) d32 += to_acc(r) * to_acc(r);

@@ -49,6 +49,7 @@ def test_default_params(lib):
     ((0, 4, 4), 1, "positive"),
     ((6, 4, 4), 3, "divisible"),
     ((6, 4, 4), 0, "levels"),
+    ((896, 896, 896), 1, "too large"),     # 3 * 897^3 nodal entries >= 2^31
 ])
 def test_create_grid_rejects_bad_arguments(lib, dims, levels, msg):
     from paper_2201_12931_gb300._lib import TopoParams
