@@ -7,6 +7,7 @@
 // pass, so results are bitwise reproducible run to run.
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -172,48 +173,77 @@ __global__ void k_axpy_f32(long long n, const float* __restrict__ d, double* __r
 
 // ---- dense coarse solve --------------------------------------------------
 
-__global__ void k_potrf_diag(double* __restrict__ A, int npad, int kb, int* info) {
-    __shared__ double s[TB][TB + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long base = (long long)kb * TB;
-    s[ty][tx] = A[(base + ty) * npad + base + tx];
-    for (int j = 0; j < TB; ++j) {
-        __syncthreads();
-        if (ty == j && tx == j) {
-            double d = s[j][j];
-            if (!(d > 0.0) || !isfinite(d)) {
-                atomicCAS(info, 0, (int)(base + j) + 1);
-                d = 1.0;
-            }
-            s[j][j] = sqrt(d);
-        }
-        __syncthreads();
-        if (tx == j && ty > j) s[ty][j] /= s[j][j];
-        __syncthreads();
-        if (tx > j && ty >= tx) s[ty][tx] -= s[ty][j] * s[tx][j];
-    }
-    __syncthreads();
-    A[(base + ty) * npad + base + tx] = (tx <= ty) ? s[ty][tx] : 0.0;
-}
-
-// L_ib,kb = A_ib,kb L_kk^-T for every block row ib > kb (one block each)
-__global__ void k_trsm_panel(double* __restrict__ A, int npad, int kb) {
+// Cholesky of diagonal block kb in one warp: lane i holds row i in registers
+// (right-looking; column j broadcast by shuffles).  L goes back to the block
+// (zeros above the diagonal); then lane c forms column c of L_kk^-1 by forward
+// substitution from the factor staged in shared memory, into Dk (block kb:
+// TB x TB row-major at Dk + kb TB^2), so that the panel and inverse steps are
+// plain block products.  A non-positive or non-finite pivot sets info to its
+// row + 1 (first one wins) and continues with pivot 1.
+__global__ void __launch_bounds__(TB) k_potrf_diag(double* __restrict__ A, int npad, int kb, int* info,
+                                                   double* __restrict__ Dk) {
     __shared__ double sL[TB][TB + 1];
-    __shared__ double sA[TB][TB + 1];
-    const int ib = kb + 1 + blockIdx.x;
-    const int r = threadIdx.x;
-    const long long rb = (long long)ib * TB, cb = (long long)kb * TB;
+    __shared__ double sR[TB];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const long long base = (long long)kb * TB;
+    double a[TB];
+#pragma unroll
+    for (int c = 0; c < TB; ++c) a[c] = A[(base + lane) * npad + base + c];
+#pragma unroll
+    for (int j = 0; j < TB; ++j) {
+        double d = __shfl_sync(full, a[j], j);
+        if (!(d > 0.0) || !isfinite(d)) {
+            if (lane == 0) atomicCAS(info, 0, (int)(base + j) + 1);
+            d = 1.0;
+        }
+        const double ljj = sqrt(d), rj = 1.0 / ljj;
+        if (lane == j) {
+            a[j] = ljj;
+            sR[j] = rj;
+        } else if (lane > j) {
+            a[j] *= rj;
+        }
+#pragma unroll
+        for (int k = j + 1; k < TB; ++k) {
+            const double lkj = __shfl_sync(full, a[j], k);
+            if (lane >= k) a[k] -= a[j] * lkj;
+        }
+    }
+#pragma unroll
     for (int c = 0; c < TB; ++c) {
-        sL[r][c] = A[(cb + r) * npad + cb + c];
-        sA[r][c] = A[(rb + r) * npad + cb + c];
+        const double v = (c <= lane) ? a[c] : 0.0;
+        sL[lane][c] = v;
+        A[(base + lane) * npad + base + c] = v;
     }
     __syncwarp();
-    for (int j = 0; j < TB; ++j) {
-        double v = sA[r][j];
-        for (int c = 0; c < j; ++c) v -= sA[r][c] * sL[j][c];
-        sA[r][j] = v / sL[j][j];
+    double x[TB];
+#pragma unroll
+    for (int r = 0; r < TB; ++r) {
+        double v = (r == lane) ? 1.0 : 0.0;
+#pragma unroll
+        for (int t = 0; t < r; ++t) v -= sL[r][t] * x[t];
+        x[r] = v * sR[r];
     }
-    for (int c = 0; c < TB; ++c) A[(rb + r) * npad + cb + c] = sA[r][c];
+    double* D = Dk + base * TB;
+#pragma unroll
+    for (int r = 0; r < TB; ++r) D[r * TB + lane] = x[r];
+}
+
+// L_ib,kb = A_ib,kb L_kk^-T for the block rows ib = kb+1+blockIdx.x (TB x TB threads)
+__global__ void k_trsm_panel(double* __restrict__ A, int npad, int kb, const double* __restrict__ Dk) {
+    __shared__ double sA[TB][TB + 1];
+    __shared__ double sI[TB][TB + 1];
+    const int ib = kb + 1 + blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long rb = (long long)ib * TB, cb = (long long)kb * TB;
+    sA[ty][tx] = A[(rb + ty) * npad + cb + tx];
+    sI[ty][tx] = Dk[cb * TB + ty * TB + tx];
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < TB; ++t) s += sA[ty][t] * sI[tx][t];
+    A[(rb + ty) * npad + cb + tx] = s;
 }
 
 // A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib
@@ -244,26 +274,20 @@ __global__ void k_identity(double* __restrict__ W, int npad) {
     W[i] = ((i / npad) == (i % npad)) ? 1.0 : 0.0;
 }
 
-// W_kb,jb = L_kk^-1 B_kb,jb for jb <= kb (forward substitution, thread per column)
-__global__ void k_trsm_rows(const double* __restrict__ L, double* __restrict__ W, int npad, int kb) {
-    __shared__ double sL[TB][TB + 1];
+// W_kb,jb = L_kk^-1 B_kb,jb for jb = blockIdx.x <= kb (TB x TB threads)
+__global__ void k_trsm_rows(double* __restrict__ W, int npad, int kb, const double* __restrict__ Dk) {
+    __shared__ double sB[TB][TB + 1];
+    __shared__ double sI[TB][TB + 1];
     const int jb = blockIdx.x;
-    const int col = threadIdx.x;
-    const long long rb = (long long)kb * TB;
-    for (int r = 0; r < TB; ++r) sL[r][col] = L[(rb + r) * npad + rb + col];
-    __syncwarp();
-    double x[TB];
-#pragma unroll
-    for (int r = 0; r < TB; ++r) x[r] = W[(rb + r) * npad + (long long)jb * TB + col];
-#pragma unroll
-    for (int r = 0; r < TB; ++r) {
-        double v = x[r];
-#pragma unroll
-        for (int c = 0; c < r; ++c) v -= sL[r][c] * x[c];
-        x[r] = v / sL[r][r];
-    }
-#pragma unroll
-    for (int r = 0; r < TB; ++r) W[(rb + r) * npad + (long long)jb * TB + col] = x[r];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long rb = (long long)kb * TB, cb = (long long)jb * TB;
+    sB[ty][tx] = W[(rb + ty) * npad + cb + tx];
+    sI[ty][tx] = Dk[rb * TB + ty * TB + tx];
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < TB; ++t) s += sI[ty][t] * sB[t][tx];
+    W[(rb + ty) * npad + cb + tx] = s;
 }
 
 // B_ib,jb -= L_ib,kb W_kb,jb for ib > kb, jb <= kb
@@ -377,15 +401,22 @@ void fill(const Ctx& c, long long n, double* v, double value) {
     TOPO_LAUNCH_CHECK(c);
 }
 
-void chol_factor(const Ctx& c, double* A, int npad, int* info) {
-    const int nb = npad / TB;
+// Blocks of a banded matrix (A_ij = 0 for |i - j| > band) that can be nonzero
+// below the diagonal block of block column kb: block rows kb+1 .. kb+bb.
+inline int band_blocks(int band) { return (band + TB - 1) / TB; }
+
+void chol_factor(const Ctx& c, double* A, int npad, int band, int* info, double* Dk) {
+    // the Cholesky factor of a banded matrix keeps its band, so the panel and
+    // the trailing update of step kb touch only the bb block rows below it;
+    // the blocks left out are zero in A and L alike
+    const int nb = npad / TB, bb = band_blocks(band);
     cudaMemsetAsync(info, 0, sizeof(int), c.s);
     for (int kb = 0; kb < nb; ++kb) {
-        k_potrf_diag<<<1, dim3(TB, TB), 0, c.s>>>(A, npad, kb, info);
+        k_potrf_diag<<<1, TB, 0, c.s>>>(A, npad, kb, info, Dk);
         TOPO_LAUNCH_CHECK(c);
-        const int m = nb - kb - 1;
+        const int m = std::min(nb - kb - 1, bb);
         if (m > 0) {
-            k_trsm_panel<<<m, TB, 0, c.s>>>(A, npad, kb);
+            k_trsm_panel<<<m, dim3(TB, TB), 0, c.s>>>(A, npad, kb, Dk);
             TOPO_LAUNCH_CHECK(c);
             k_syrk<<<m * (m + 1) / 2, dim3(TB, TB), 0, c.s>>>(A, npad, kb);
             TOPO_LAUNCH_CHECK(c);
@@ -393,15 +424,17 @@ void chol_factor(const Ctx& c, double* A, int npad, int* info) {
     }
 }
 
-void tri_inverse(const Ctx& c, const double* L, double* W, int npad) {
-    const int nb = npad / TB;
+void tri_inverse(const Ctx& c, const double* L, double* W, int npad, int band, const double* Dk) {
+    // W = L^-1 is dense lower triangular; L_ib,kb vanishes beyond the band,
+    // so the update after block row kb reaches only the bb block rows below
+    const int nb = npad / TB, bb = band_blocks(band);
     const long long n2 = (long long)npad * npad;
     k_identity<<<grid_for(n2, 256), 256, 0, c.s>>>(W, npad);
     TOPO_LAUNCH_CHECK(c);
     for (int kb = 0; kb < nb; ++kb) {
-        k_trsm_rows<<<kb + 1, TB, 0, c.s>>>(L, W, npad, kb);
+        k_trsm_rows<<<kb + 1, dim3(TB, TB), 0, c.s>>>(W, npad, kb, Dk);
         TOPO_LAUNCH_CHECK(c);
-        const int m = nb - kb - 1;
+        const int m = std::min(nb - kb - 1, bb);
         if (m > 0) {
             k_gemm_update<<<dim3(kb + 1, m), dim3(TB, TB), 0, c.s>>>(L, W, npad, kb);
             TOPO_LAUNCH_CHECK(c);

@@ -163,7 +163,7 @@ void free_all(topo_grid* h) {
         F(l.ha); F(l.hb); F(l.Ke64); F(l.Ke32);
     }
     F(h->cs.A); F(h->cs.W64); F(h->cs.WT64); F(h->cs.W32); F(h->cs.WT32); F(h->cs.y64); F(h->cs.y32);
-    F(h->cs.info);
+    F(h->cs.info); F(h->cs.Dk);
     F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
     F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
     F(h->K0d); F(h->K0f);
@@ -208,16 +208,21 @@ topo_status ensure_coarse(topo_grid* h) {
         ALLOC(h, cs.y64, cs.npad);
         ALLOC(h, cs.y32, cs.npad);
         ALLOC(h, cs.info, 1);
+        ALLOC(h, cs.Dk, (size_t)cs.npad * 32);
     }
     assemble_coarse(c, lc.g, h->K0d, lc.E64, h->prm.homogenize == 2 && h->L > 1 ? lc.Ke64 : nullptr, lc.mask, cs.A,
                     cs.npad);
-    chol_factor(c, cs.A, cs.npad, cs.info);
+    // half-bandwidth of the coarsest matrix: DOFs of nodes up to one step
+    // apart in each direction (node order x fastest, 3 DOFs per node)
+    const int NXc = lc.g.nx + 1, NYc = lc.g.ny + 1;
+    const int band = 3 * (1 + NXc + NXc * NYc) + 2;
+    chol_factor(c, cs.A, cs.npad, band, cs.info, cs.Dk);
     int info = 0;
     CK(h, cudaMemcpyAsync(&info, cs.info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (info != 0)
         return fail(h, TOPO_BREAKDOWN, "coarsest-grid matrix not positive definite at row " + std::to_string(info - 1));
-    tri_inverse(c, cs.A, cs.W64, cs.npad);
+    tri_inverse(c, cs.A, cs.W64, cs.npad, band, cs.Dk);
     transpose_dense(c, cs.W64, cs.WT64, cs.npad);
     const long long n2 = (long long)cs.npad * cs.npad;
     convert<double, float>(c, n2, cs.W64, cs.W32);

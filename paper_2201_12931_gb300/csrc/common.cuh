@@ -81,6 +81,7 @@ struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
     double* y64 = nullptr;    // temporaries of length npad
     float* y32 = nullptr;
     int* info = nullptr;      // device: first non-positive pivot + 1 (0 = ok)
+    double* Dk = nullptr;     // inverses of the 32 x 32 diagonal blocks of L (npad x 32)
 };
 
 struct PcgGraph {             // one captured PCG iteration (precond, beta, p, K p, alpha, x/r update)
@@ -261,8 +262,11 @@ template <typename T>
 void zero(const Ctx& c, long long n, T* v);
 void fill(const Ctx& c, long long n, double* v, double value);
 // dense coarse solve
-void chol_factor(const Ctx& c, double* A, int npad, int* info);
-void tri_inverse(const Ctx& c, const double* L, double* W, int npad);
+// band: half-bandwidth of A in entries (npad for a dense matrix); Dk
+// (npad x 32 doubles) receives the inverses of the 32 x 32 diagonal blocks of
+// L, which tri_inverse reads
+void chol_factor(const Ctx& c, double* A, int npad, int band, int* info, double* Dk);
+void tri_inverse(const Ctx& c, const double* L, double* W, int npad, int band, const double* Dk);
 void transpose_dense(const Ctx& c, const double* W, double* WT, int npad);
 template <typename T>
 void coarse_apply(const Ctx& c, int n, int npad, const T* W, const T* WT, const T* rhs, T* y, T* out);
