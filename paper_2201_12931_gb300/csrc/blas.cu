@@ -173,72 +173,81 @@ __global__ void k_axpy_f32(long long n, const float* __restrict__ d, double* __r
 
 // ---- dense coarse solve --------------------------------------------------
 
-// Cholesky of diagonal block kb in one warp: lane i holds row i in registers
-// (right-looking; column j broadcast by shuffles).  L goes back to the block
-// (zeros above the diagonal); then lane c forms column c of L_kk^-1 by forward
-// substitution from the factor staged in shared memory, into Dk (block kb:
-// TB x TB row-major at Dk + kb TB^2), so that the panel and inverse steps are
-// plain block products.  A non-positive or non-finite pivot sets info to its
-// row + 1 (first one wins) and continues with pivot 1.
-__global__ void __launch_bounds__(TB) k_potrf_diag(double* __restrict__ A, int npad, int kb, int* info,
-                                                   double* __restrict__ Dk) {
-    __shared__ double sL[TB][TB + 1];
+// The dense coarse factorization is a chain of small steps, and FP64
+// arithmetic runs on a narrow pipe (1/64 of the FP32 rate on this GPU): the
+// kernels below spread each step's FP64 work over as many SMs as it allows,
+// in strips of kStrip rows (or columns) of a 32 x 32 tile per CTA of 128
+// threads, instead of one tile per CTA.
+constexpr int kStrip = 4;
+
+// Cholesky of diagonal block kb by one CTA of 128 threads (right-looking, in
+// shared memory; the pivot by one thread: rs = rsqrt(d), L_jj = d rs), then
+// L_kk^-1 by forward elimination (row j of X = B_j / L_jj, then
+// B_i -= L_ij X_j for the rows below).  L goes back to the block (zeros above
+// the diagonal), L_kk^-1 to Dk (block kb: TB x TB row-major at Dk + kb TB^2).
+// A non-positive or non-finite pivot sets info to its row + 1 (first one
+// wins) and continues with pivot 1.
+__global__ void __launch_bounds__(128) k_potrf_diag(double* __restrict__ A, int npad, int kb, int* info,
+                                                    double* __restrict__ Dk) {
+    __shared__ double sA[TB][TB + 1];
+    __shared__ double sX[TB][TB + 1];
     __shared__ double sR[TB];
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x;
     const long long base = (long long)kb * TB;
-    double a[TB];
-#pragma unroll
-    for (int c = 0; c < TB; ++c) a[c] = A[(base + lane) * npad + base + c];
-#pragma unroll
+    for (int e = tid; e < TB * TB; e += 128) {
+        const int r = e / TB, c = e % TB;
+        sA[r][c] = A[(base + r) * npad + base + c];
+        sX[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
     for (int j = 0; j < TB; ++j) {
-        double d = __shfl_sync(full, a[j], j);
-        if (!(d > 0.0) || !isfinite(d)) {
-            if (lane == 0) atomicCAS(info, 0, (int)(base + j) + 1);
-            d = 1.0;
+        if (tid == 0) {
+            double d = sA[j][j];
+            if (!(d > 0.0) || !isfinite(d)) {
+                atomicCAS(info, 0, (int)(base + j) + 1);
+                d = 1.0;
+            }
+            const double rs = rsqrt(d);
+            sA[j][j] = d * rs;
+            sR[j] = rs;
         }
-        const double ljj = sqrt(d), rj = 1.0 / ljj;
-        if (lane == j) {
-            a[j] = ljj;
-            sR[j] = rj;
-        } else if (lane > j) {
-            a[j] *= rj;
+        __syncthreads();
+        if (tid > j && tid < TB) sA[tid][j] *= sR[j];
+        __syncthreads();
+        for (int e = tid; e < TB * TB; e += 128) {
+            const int i = e / TB, k = e % TB;
+            if (k > j && k <= i) sA[i][k] -= sA[i][j] * sA[k][j];
         }
-#pragma unroll
-        for (int k = j + 1; k < TB; ++k) {
-            const double lkj = __shfl_sync(full, a[j], k);
-            if (lane >= k) a[k] -= a[j] * lkj;
-        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int c = 0; c < TB; ++c) {
-        const double v = (c <= lane) ? a[c] : 0.0;
-        sL[lane][c] = v;
-        A[(base + lane) * npad + base + c] = v;
-    }
-    __syncwarp();
-    double x[TB];
-#pragma unroll
-    for (int r = 0; r < TB; ++r) {
-        double v = (r == lane) ? 1.0 : 0.0;
-#pragma unroll
-        for (int t = 0; t < r; ++t) v -= sL[r][t] * x[t];
-        x[r] = v * sR[r];
+    for (int j = 0; j < TB; ++j) {
+        if (tid <= j) sX[j][tid] *= sR[j];
+        __syncthreads();
+        for (int e = tid; e < TB * TB; e += 128) {
+            const int i = e / TB, c = e % TB;
+            if (i > j && c <= j) sX[i][c] -= sA[i][j] * sX[j][c];
+        }
+        __syncthreads();
     }
     double* D = Dk + base * TB;
-#pragma unroll
-    for (int r = 0; r < TB; ++r) D[r * TB + lane] = x[r];
+    for (int e = tid; e < TB * TB; e += 128) {
+        const int r = e / TB, c = e % TB;
+        A[(base + r) * npad + base + c] = (c <= r) ? sA[r][c] : 0.0;
+        D[e] = sX[r][c];
+    }
 }
 
-// L_ib,kb = A_ib,kb L_kk^-T for the block rows ib = kb+1+blockIdx.x (TB x TB threads)
-__global__ void k_trsm_panel(double* __restrict__ A, int npad, int kb, const double* __restrict__ Dk) {
-    __shared__ double sA[TB][TB + 1];
+// L_ib,kb = A_ib,kb L_kk^-T: block row ib = kb+1+blockIdx.y, its rows
+// kStrip*blockIdx.x .. +kStrip (threads: 32 columns x kStrip rows)
+__global__ void __launch_bounds__(128) k_trsm_panel(double* __restrict__ A, int npad, int kb,
+                                                    const double* __restrict__ Dk) {
     __shared__ double sI[TB][TB + 1];
-    const int ib = kb + 1 + blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long rb = (long long)ib * TB, cb = (long long)kb * TB;
+    __shared__ double sA[kStrip][TB + 1];
+    const int ib = kb + 1 + blockIdx.y, r0 = kStrip * blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TB + tx;
+    const long long rb = (long long)ib * TB + r0, cb = (long long)kb * TB;
+    for (int e = tid; e < TB * TB; e += 128) sI[e / TB][e % TB] = Dk[cb * TB + e];
     sA[ty][tx] = A[(rb + ty) * npad + cb + tx];
-    sI[ty][tx] = Dk[cb * TB + ty * TB + tx];
     __syncthreads();
     double s = 0.0;
 #pragma unroll 8
@@ -246,25 +255,26 @@ __global__ void k_trsm_panel(double* __restrict__ A, int npad, int kb, const dou
     A[(rb + ty) * npad + cb + tx] = s;
 }
 
-// A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib
-__global__ void k_syrk(double* __restrict__ A, int npad, int kb) {
-    __shared__ double sI[TB][TB + 1];
+// A_ib,jb -= L_ib,kb L_jb,kb^T for kb < jb <= ib (pair blockIdx.y), rows
+// kStrip*blockIdx.x .. +kStrip of the tile
+__global__ void __launch_bounds__(128) k_syrk(double* __restrict__ A, int npad, int kb) {
+    __shared__ double sI[kStrip][TB + 1];
     __shared__ double sJ[TB][TB + 1];
-    const int t = blockIdx.x;
+    const int t = blockIdx.y;
     int ii = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
     while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
     while (ii * (ii + 1) / 2 > t) --ii;
     const int jj = t - ii * (ii + 1) / 2;
-    const int ib = kb + 1 + ii, jb = kb + 1 + jj;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long cb = (long long)kb * TB;
-    sI[ty][tx] = A[((long long)ib * TB + ty) * npad + cb + tx];
-    sJ[ty][tx] = A[((long long)jb * TB + ty) * npad + cb + tx];
+    const int ib = kb + 1 + ii, jb = kb + 1 + jj, r0 = kStrip * blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TB + tx;
+    const long long cb = (long long)kb * TB, rb = (long long)ib * TB + r0, jr = (long long)jb * TB;
+    sI[ty][tx] = A[(rb + ty) * npad + cb + tx];
+    for (int e = tid; e < TB * TB; e += 128) sJ[e / TB][e % TB] = A[(jr + e / TB) * npad + cb + e % TB];
     __syncthreads();
     double s = 0.0;
 #pragma unroll 8
     for (int c = 0; c < TB; ++c) s += sI[ty][c] * sJ[tx][c];
-    A[((long long)ib * TB + ty) * npad + (long long)jb * TB + tx] -= s;
+    A[(rb + ty) * npad + jr + tx] -= s;
 }
 
 __global__ void k_identity(double* __restrict__ W, int npad) {
@@ -274,15 +284,17 @@ __global__ void k_identity(double* __restrict__ W, int npad) {
     W[i] = ((i / npad) == (i % npad)) ? 1.0 : 0.0;
 }
 
-// W_kb,jb = L_kk^-1 B_kb,jb for jb = blockIdx.x <= kb (TB x TB threads)
-__global__ void k_trsm_rows(double* __restrict__ W, int npad, int kb, const double* __restrict__ Dk) {
-    __shared__ double sB[TB][TB + 1];
+// W_kb,jb = L_kk^-1 B_kb,jb for jb = blockIdx.y <= kb, its columns
+// kStrip*blockIdx.x .. +kStrip (threads: kStrip columns x 32 rows)
+__global__ void __launch_bounds__(128) k_trsm_rows(double* __restrict__ W, int npad, int kb,
+                                                   const double* __restrict__ Dk) {
     __shared__ double sI[TB][TB + 1];
-    const int jb = blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long rb = (long long)kb * TB, cb = (long long)jb * TB;
+    __shared__ double sB[TB][kStrip + 1];
+    const int jb = blockIdx.y, c0 = kStrip * blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kStrip + tx;
+    const long long rb = (long long)kb * TB, cb = (long long)jb * TB + c0;
+    for (int e = tid; e < TB * TB; e += 128) sI[e / TB][e % TB] = Dk[rb * TB + e];
     sB[ty][tx] = W[(rb + ty) * npad + cb + tx];
-    sI[ty][tx] = Dk[rb * TB + ty * TB + tx];
     __syncthreads();
     double s = 0.0;
 #pragma unroll 8
@@ -290,20 +302,22 @@ __global__ void k_trsm_rows(double* __restrict__ W, int npad, int kb, const doub
     W[(rb + ty) * npad + cb + tx] = s;
 }
 
-// B_ib,jb -= L_ib,kb W_kb,jb for ib > kb, jb <= kb
-__global__ void k_gemm_update(const double* __restrict__ L, double* __restrict__ W, int npad, int kb) {
-    __shared__ double sL[TB][TB + 1];
+// B_ib,jb -= L_ib,kb W_kb,jb for jb = blockIdx.y <= kb, ib = kb+1+blockIdx.z,
+// rows kStrip*blockIdx.x .. +kStrip of the tile
+__global__ void __launch_bounds__(128) k_gemm_update(const double* __restrict__ L, double* __restrict__ W, int npad,
+                                                     int kb) {
+    __shared__ double sL[kStrip][TB + 1];
     __shared__ double sW[TB][TB + 1];
-    const int ib = kb + 1 + blockIdx.y, jb = blockIdx.x;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const long long kbase = (long long)kb * TB;
-    sL[ty][tx] = L[((long long)ib * TB + ty) * npad + kbase + tx];
-    sW[ty][tx] = W[(kbase + ty) * npad + (long long)jb * TB + tx];
+    const int jb = blockIdx.y, ib = kb + 1 + blockIdx.z, r0 = kStrip * blockIdx.x;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TB + tx;
+    const long long kbase = (long long)kb * TB, rb = (long long)ib * TB + r0, cb = (long long)jb * TB;
+    sL[ty][tx] = L[(rb + ty) * npad + kbase + tx];
+    for (int e = tid; e < TB * TB; e += 128) sW[e / TB][e % TB] = W[(kbase + e / TB) * npad + cb + e % TB];
     __syncthreads();
     double s = 0.0;
 #pragma unroll 8
     for (int c = 0; c < TB; ++c) s += sL[ty][c] * sW[c][tx];
-    W[((long long)ib * TB + ty) * npad + (long long)jb * TB + tx] -= s;
+    W[(rb + ty) * npad + cb + tx] -= s;
 }
 
 __global__ void k_transpose(const double* __restrict__ W, double* __restrict__ WT, int npad) {
@@ -412,13 +426,13 @@ void chol_factor(const Ctx& c, double* A, int npad, int band, int* info, double*
     const int nb = npad / TB, bb = band_blocks(band);
     cudaMemsetAsync(info, 0, sizeof(int), c.s);
     for (int kb = 0; kb < nb; ++kb) {
-        k_potrf_diag<<<1, TB, 0, c.s>>>(A, npad, kb, info, Dk);
+        k_potrf_diag<<<1, 128, 0, c.s>>>(A, npad, kb, info, Dk);
         TOPO_LAUNCH_CHECK(c);
         const int m = std::min(nb - kb - 1, bb);
         if (m > 0) {
-            k_trsm_panel<<<m, dim3(TB, TB), 0, c.s>>>(A, npad, kb, Dk);
+            k_trsm_panel<<<dim3(TB / kStrip, m), dim3(TB, kStrip), 0, c.s>>>(A, npad, kb, Dk);
             TOPO_LAUNCH_CHECK(c);
-            k_syrk<<<m * (m + 1) / 2, dim3(TB, TB), 0, c.s>>>(A, npad, kb);
+            k_syrk<<<dim3(TB / kStrip, m * (m + 1) / 2), dim3(TB, kStrip), 0, c.s>>>(A, npad, kb);
             TOPO_LAUNCH_CHECK(c);
         }
     }
@@ -432,11 +446,11 @@ void tri_inverse(const Ctx& c, const double* L, double* W, int npad, int band, c
     k_identity<<<grid_for(n2, 256), 256, 0, c.s>>>(W, npad);
     TOPO_LAUNCH_CHECK(c);
     for (int kb = 0; kb < nb; ++kb) {
-        k_trsm_rows<<<kb + 1, dim3(TB, TB), 0, c.s>>>(W, npad, kb, Dk);
+        k_trsm_rows<<<dim3(TB / kStrip, kb + 1), dim3(kStrip, TB), 0, c.s>>>(W, npad, kb, Dk);
         TOPO_LAUNCH_CHECK(c);
         const int m = std::min(nb - kb - 1, bb);
         if (m > 0) {
-            k_gemm_update<<<dim3(kb + 1, m), dim3(TB, TB), 0, c.s>>>(L, W, npad, kb);
+            k_gemm_update<<<dim3(TB / kStrip, kb + 1, m), dim3(TB, kStrip), 0, c.s>>>(L, W, npad, kb);
             TOPO_LAUNCH_CHECK(c);
         }
     }

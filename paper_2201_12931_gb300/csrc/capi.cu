@@ -183,6 +183,8 @@ void free_all(topo_grid* h) {
         if (h->graph32[q].exec) cudaGraphExecDestroy(h->graph32[q].exec);
         h->graph64[q].exec = h->graph32[q].exec = nullptr;
     }
+    if (h->coarse_graph.exec) cudaGraphExecDestroy(h->coarse_graph.exec);
+    h->coarse_graph.exec = nullptr;
     for (auto e : h->prof_ev) cudaEventDestroy(e);
     h->prof_ev.clear();
 }
@@ -192,7 +194,6 @@ void free_all(topo_grid* h) {
 topo_status ensure_coarse(topo_grid* h) {
     if (!h->coarse_dirty) return TOPO_OK;
     if (!h->have_density || !h->have_bc) return fail(h, TOPO_BADARG, "density and boundary conditions must be set");
-    const Ctx c = h->ctx();
     Level& lc = h->lev[h->L - 1];
     Coarse& cs = h->cs;
     if (cs.n > kMaxCoarseDofs)
@@ -210,23 +211,38 @@ topo_status ensure_coarse(topo_grid* h) {
         ALLOC(h, cs.info, 1);
         ALLOC(h, cs.Dk, (size_t)cs.npad * 32);
     }
-    assemble_coarse(c, lc.g, h->K0d, lc.E64, h->prm.homogenize == 2 && h->L > 1 ? lc.Ke64 : nullptr, lc.mask, cs.A,
-                    cs.npad);
     // half-bandwidth of the coarsest matrix: DOFs of nodes up to one step
     // apart in each direction (node order x fastest, 3 DOFs per node)
     const int NXc = lc.g.nx + 1, NYc = lc.g.ny + 1;
     const int band = 3 * (1 + NXc + NXc * NYc) + 2;
-    chol_factor(c, cs.A, cs.npad, band, cs.info, cs.Dk);
+    // assembly, Cholesky, L^-1, its transpose and FP32 copies: a fixed
+    // sequence of a few hundred small launches, captured once per handle into
+    // a CUDA graph and replayed for each new density (the pointers do not
+    // change); the pivot check reads info after the whole sequence
+    auto body = [&]() {
+        const Ctx cc = h->ctx();
+        assemble_coarse(cc, lc.g, h->K0d, lc.E64, h->prm.homogenize == 2 && h->L > 1 ? lc.Ke64 : nullptr, lc.mask,
+                        cs.A, cs.npad);
+        chol_factor(cc, cs.A, cs.npad, band, cs.info, cs.Dk);
+        tri_inverse(cc, cs.A, cs.W64, cs.npad, band, cs.Dk);
+        transpose_dense(cc, cs.W64, cs.WT64, cs.npad);
+        const long long n2 = (long long)cs.npad * cs.npad;
+        convert<double, float>(cc, n2, cs.W64, cs.W32);
+        convert<double, float>(cc, n2, cs.WT64, cs.WT32);
+    };
+    PcgGraph& gr = h->coarse_graph;
+    if (h->prm.graphs != 0 && !gr.exec && !gr.failed) capture_launches(h, gr, body);
+    if (gr.exec) {
+        CK(h, cudaGraphLaunch(gr.exec, h->stream));
+        h->launches += gr.launches;
+    } else {
+        body();
+    }
     int info = 0;
     CK(h, cudaMemcpyAsync(&info, cs.info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (info != 0)
         return fail(h, TOPO_BREAKDOWN, "coarsest-grid matrix not positive definite at row " + std::to_string(info - 1));
-    tri_inverse(c, cs.A, cs.W64, cs.npad, band, cs.Dk);
-    transpose_dense(c, cs.W64, cs.WT64, cs.npad);
-    const long long n2 = (long long)cs.npad * cs.npad;
-    convert<double, float>(c, n2, cs.W64, cs.W32);
-    convert<double, float>(c, n2, cs.WT64, cs.WT32);
     h->coarse_dirty = false;
     return TOPO_OK;
 }
@@ -311,6 +327,16 @@ topo_status check_handle(topo_grid* h) {
 }
 
 }  // namespace
+
+void topo::ensure_dinv64(topo_grid* h) {
+    if (!h->dinv64_dirty) return;
+    const Ctx c = h->ctx();
+    for (int l = 0; l < h->L; ++l) {
+        Level& lv = h->lev[l];
+        diag_inverse<double>(c, lv.g, lv.E64, h->mk64->kdiag, lv.Dinv64);
+    }
+    h->dinv64_dirty = false;
+}
 
 void topo::set_global_error(const std::string& msg) { g_create_err = msg; }
 
@@ -531,10 +557,11 @@ static topo_status set_density_from(topo_handle h, const double* rho, cudaMemcpy
             }
         }
     }
-    for (int l = 0; l < h->L; ++l) {   // Jacobi diagonals from the final moduli of every level
+    for (int l = 0; l < h->L; ++l) {   // FP32 Jacobi diagonals from the final moduli of every level
         Level& lv = h->lev[l];
-        diag_inverse(c, lv.g, lv.E64, h->mk64->kdiag, lv.Dinv64, lv.Dinv32);
+        diag_inverse<float>(c, lv.g, lv.E32, h->mk32->kdiag, lv.Dinv32);
     }
+    h->dinv64_dirty = true;   // FP64 ones on demand (ensure_dinv64): FP64 division runs on the slow FP64 pipe
     if (h->prm.homogenize == 2) {
         for (int l = 1; l < h->L; ++l) {
             Level& lv = h->lev[l];
@@ -937,6 +964,7 @@ topo_status topo_vcycle(topo_handle h, int precision, const double* r_dev, doubl
     Level& l0 = h->lev[0];
     const long long n = 3 * l0.g.nn;
     if (precision == TOPO_FP64) {
+        ensure_dinv64(h);
         vcycle<double>(h, 0, r_dev, z_dev, l0.v64.a, nullptr);
     } else if (precision == TOPO_MIXED_BF16) {
         const Ctx c = h->ctx();

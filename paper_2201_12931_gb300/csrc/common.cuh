@@ -131,6 +131,7 @@ struct topo_grid {
     double* dtmp = nullptr;         // device scratch scalars
     int* dflag = nullptr;           // device: density out of [0,1] seen
     bool coarse_dirty = true;
+    bool dinv64_dirty = true;       // FP64 D^-1 of the levels: formed when an FP64 V-cycle first needs it
     bool x_zero = true;             // warm start is u = 0 (initial residual is f)
     // launch timing of fine-level operator kernels (topo_profile_enable)
     bool prof_on = false;
@@ -143,6 +144,7 @@ struct topo_grid {
     bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false, bf16_ready = false;
     long long launches = 0;
     topo::PcgGraph graph64[2], graph32[2];   // captured PCG iterations per precision and direction buffer
+    topo::PcgGraph coarse_graph;            // captured coarsest-grid assembly, factorization and inverse
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
     topo_solve_stats stats{};
     std::string err;
@@ -230,8 +232,10 @@ void prolong_add_bf16(const Ctx& c, const Geom& gf, const uint8_t* maskf, const 
                       bf16* uf);
 // coarse = scale * mean of the 8 children (densities: scale 1; moduli: scale 2)
 void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c, double scale);
-// per node D^-1 = 1 / (kdiag * sum of E over the <= 8 elements around it)
-void diag_inverse(const Ctx& c, const Geom& g, const double* E, double kdiag, double* Dinv64, float* Dinv32);
+// per node D^-1 = 1 / (kdiag * sum of E over the <= 8 elements around it),
+// in the precision of E (indices in 32 bits: the grid limit of create_grid)
+template <typename T>
+void diag_inverse(const Ctx& c, const Geom& g, const T* E, T kdiag, T* Dinv);
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0,
                  double Emin, double penal, double* E64, float* E32, int* bad_flag);
 void mask_from_dofs(const Ctx& c, long long nn, const uint8_t* fixed_dofs, uint8_t* mask);

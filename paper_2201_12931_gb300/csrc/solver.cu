@@ -279,6 +279,8 @@ static void capture_graph(topo_grid* h, PcgGraph& gr, F&& body) {
     if (graph) cudaGraphDestroy(graph);
 }
 
+void capture_launches(topo_grid* h, PcgGraph& gr, const std::function<void()>& body) { capture_graph(h, gr, body); }
+
 // copies the scalars to the pinned mirror and waits for them
 static void fetch_scalars(topo_grid* h) {
     cudaMemcpyAsync(h->host_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream);
@@ -463,6 +465,7 @@ double current_relres(topo_grid* h) {
 }
 
 int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres) {
+    ensure_dinv64(h);
     const double ff = h->host_sc[6];
     double rr_true = residual64(h);
     int status = TOPO_OK, it = 0, restarts = 0;

@@ -1,5 +1,7 @@
 // Host-side solver entry points shared by capi.cu and solver.cu.
 #pragma once
+#include <functional>
+
 #include "common.cuh"
 
 namespace topo {
@@ -15,7 +17,12 @@ int vcycle(topo_grid* h, int l, const T* f, T* out, T* tmp, double* dot);
 // from the level's v32.a (used for the residual).
 int vcycle_bf16(topo_grid* h, int l, const float* f, float* out, double* dot);
 int solve_fp64(topo_grid* h, double tol, int max_it, int* iters, double* relres);
+// FP64 D^-1 of every level (read by the FP64 V-cycle), formed once per density
+void ensure_dinv64(topo_grid* h);
 int solve_mixed(topo_grid* h, double tol, int max_it, int* iters, double* relres);
 // ||f - K x|| / ||f|| of the current iterate in FP64 (1 when x is known to be 0)
 double current_relres(topo_grid* h);
+// Captures the launches of body() (which enqueues on h->stream) into gr on a
+// private stream; gr.failed when capture is not possible (then launch directly)
+void capture_launches(topo_grid* h, PcgGraph& gr, const std::function<void()>& body);
 }  // namespace topo

@@ -184,26 +184,21 @@ __device__ __forceinline__ double rpow(double r, double p, int ip) {
     return pow(r, p);
 }
 
-// D^-1 of the Jacobi sweeps: node (i, j, k) sums E over the in-grid elements
-// (i-1..i, j-1..j, k-1..k) in a fixed order (E carries the level scale 2^l)
-__global__ void k_diag_inv(const double* __restrict__ E, int nx, int ny, int nz, double kdiag,
-                           double* __restrict__ D64, float* __restrict__ D32) {
-    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
-    const long long nn = (long long)NX * NY * NZ;
-    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (n >= nn) return;
-    const int i = (int)(n % NX);
-    const long long t = n / NX;
-    const int j = (int)(t % NY), k = (int)(t / NY);
-    double s = 0.0;
+// D^-1 of the first two pre-smoothing sweeps: node (i, j, k) sums E over the
+// in-grid elements (i-1..i, j-1..j, k-1..k) in a fixed order (E carries the
+// level scale 2^l); one thread per node of an x-y tile, z from the grid
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_inv(const T* __restrict__ E, int nx, int ny, int nz, T kdiag,
+                                                  T* __restrict__ D) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i > nx || j > ny) return;
+    T s = T(0);
     for (int ez = k - 1; ez <= k; ++ez)
         for (int ey = j - 1; ey <= j; ++ey)
             for (int ex = i - 1; ex <= i; ++ex)
                 if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
-                    s += E[ex + (long long)nx * (ey + (long long)ny * ez)];
-    const double d = s > 0.0 ? 1.0 / (kdiag * s) : 0.0;
-    D64[n] = d;
-    D32[n] = (float)d;
+                    s += E[ex + nx * (ey + ny * ez)];
+    D[i + (nx + 1) * (j + (ny + 1) * k)] = s > T(0) ? T(1) / (kdiag * s) : T(0);
 }
 
 __global__ void k_simp(long long ne, const double* __restrict__ rho, double scale, double E0, double Emin,
@@ -283,10 +278,14 @@ void homogenize(const Ctx& c, const Geom& gf, const double* rho_f, double* rho_c
     TOPO_LAUNCH_CHECK(c);
 }
 
-void diag_inverse(const Ctx& c, const Geom& g, const double* E, double kdiag, double* Dinv64, float* Dinv32) {
-    k_diag_inv<<<grid_for(g.nn, 256), 256, 0, c.s>>>(E, g.nx, g.ny, g.nz, kdiag, Dinv64, Dinv32);
+template <typename T>
+void diag_inverse(const Ctx& c, const Geom& g, const T* E, T kdiag, T* Dinv) {
+    const dim3 grid((g.nx + 1 + 31) / 32, (g.ny + 1 + 7) / 8, g.nz + 1);
+    k_diag_inv<T><<<grid, dim3(32, 8), 0, c.s>>>(E, g.nx, g.ny, g.nz, kdiag, Dinv);
     TOPO_LAUNCH_CHECK(c);
 }
+template void diag_inverse<double>(const Ctx&, const Geom&, const double*, double, double*);
+template void diag_inverse<float>(const Ctx&, const Geom&, const float*, float, float*);
 
 void simp_moduli(const Ctx& c, long long ne, const double* rho, double scale, double E0, double Emin, double penal,
                  double* E64, float* E32, int* bad_flag) {
