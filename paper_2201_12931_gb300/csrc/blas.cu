@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(1024) k_reduce_to(const double* __restrict__ p
     if (threadIdx.x == 0) *dst = s;
 }
 
-__global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p, int n, Scalars* sc) {
+__global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p, int n, Scalars* sc,
+                                                   double* __restrict__ hist) {
     __shared__ double sh[32];
     const double pq = sum_partials(p, n, sh);
     if (threadIdx.x == 0) {
@@ -76,6 +77,7 @@ __global__ void __launch_bounds__(1024) k_cg_alpha(const double* __restrict__ p,
             sc->alpha = 0.0;
             sc->aux = 1.0;   // breakdown flag, read by the host
         }
+        if (hist) *hist = sc->alpha;
     }
 }
 
@@ -146,6 +148,85 @@ __global__ void __launch_bounds__(256) k_update_xr(long long n, const Scalars* _
     }
     s = block_sum(s, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// r -= alpha q and per-block partial sums of r.r (as k_update_xr without x)
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_r(long long n, const Scalars* __restrict__ sc, const T* __restrict__ q,
+                                                  T* __restrict__ r, double* __restrict__ partials) {
+    __shared__ double sh[32];
+    const T a = (T)sc->alpha;
+    double s = 0.0;
+    long long i0 = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        const long long n4 = n / 4;
+        const float4* q4 = reinterpret_cast<const float4*>(q);
+        float4* r4 = reinterpret_cast<float4*>(r);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            const float4 qv = q4[i];
+            float4 rv = r4[i];
+            rv.x -= a * qv.x;
+            rv.y -= a * qv.y;
+            rv.z -= a * qv.z;
+            rv.w -= a * qv.w;
+            r4[i] = rv;
+            s += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        }
+        i0 = 4 * n4;
+    }
+    for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T ri = r[i] - a * q[i];
+        r[i] = ri;
+        s += (double)ri * (double)ri;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// x += alpha_j p_j, j = 0 .. count-1 in order: per entry the same fused
+// multiply-adds as count successive x += alpha p updates, with x read and
+// written once
+template <typename T>
+struct DirRing {
+    const T* p[kDirRing];
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_flush_x(long long n, DirRing<T> ring, const double* __restrict__ alpha,
+                                                 int count, T* __restrict__ x) {
+    T a[kDirRing];
+#pragma unroll
+    for (int j = 0; j < kDirRing; ++j) a[j] = j < count ? (T)alpha[j] : T(0);
+    long long i0 = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        const long long n4 = n / 4;
+        float4* x4 = reinterpret_cast<float4*>(x);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            float4 xv = x4[i];
+#pragma unroll
+            for (int j = 0; j < kDirRing; ++j) {
+                if (j < count) {
+                    const float4 pv = reinterpret_cast<const float4*>(ring.p[j])[i];
+                    xv.x += a[j] * pv.x;
+                    xv.y += a[j] * pv.y;
+                    xv.z += a[j] * pv.z;
+                    xv.w += a[j] * pv.w;
+                }
+            }
+            x4[i] = xv;
+        }
+        i0 = 4 * n4;
+    }
+    for (long long i = i0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T xi = x[i];
+#pragma unroll
+        for (int j = 0; j < kDirRing; ++j)
+            if (j < count) xi += a[j] * ring.p[j][i];
+        x[i] = xi;
+    }
 }
 
 template <typename T>
@@ -357,8 +438,8 @@ void reduce_to(const Ctx& c, const double* partials, int n, double* dst) {
     k_reduce_to<<<1, 1024, 0, c.s>>>(partials, n, dst);
     TOPO_LAUNCH_CHECK(c);
 }
-void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc) {
-    k_cg_alpha<<<1, 1024, 0, c.s>>>(partials, n, sc);
+void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc, double* hist) {
+    k_cg_alpha<<<1, 1024, 0, c.s>>>(partials, n, sc, hist);
     TOPO_LAUNCH_CHECK(c);
 }
 void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc) {
@@ -388,6 +469,24 @@ void cg_update_p(const Ctx& c, long long n, const Scalars* sc, const T* z, T* p)
 }
 template void cg_update_p<double>(const Ctx&, long long, const Scalars*, const double*, double*);
 template void cg_update_p<float>(const Ctx&, long long, const Scalars*, const float*, float*);
+
+template <typename T>
+void cg_update_r(const Ctx& c, long long n, const Scalars* sc, const T* q, T* r, double* partials) {
+    k_update_r<T><<<kRedBlocks, 256, 0, c.s>>>(n, sc, q, r, partials);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void cg_update_r<double>(const Ctx&, long long, const Scalars*, const double*, double*, double*);
+template void cg_update_r<float>(const Ctx&, long long, const Scalars*, const float*, float*, double*);
+
+template <typename T>
+void cg_flush_x(const Ctx& c, long long n, T* const* ring, const double* alpha, int count, T* x) {
+    DirRing<T> dr;
+    for (int j = 0; j < kDirRing; ++j) dr.p[j] = ring[j];
+    k_flush_x<T><<<grid_for(n, 256) > 8192 ? 8192 : grid_for(n, 256), 256, 0, c.s>>>(n, dr, alpha, count, x);
+    TOPO_LAUNCH_CHECK(c);
+}
+template void cg_flush_x<double>(const Ctx&, long long, double* const*, const double*, int, double*);
+template void cg_flush_x<float>(const Ctx&, long long, float* const*, const double*, int, float*);
 
 template <typename S, typename D>
 void convert(const Ctx& c, long long n, const S* src, D* dst) {

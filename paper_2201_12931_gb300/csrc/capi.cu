@@ -127,6 +127,7 @@ topo_status alloc_precision(topo_grid* h, bool fp64) {
         ALLOC(h, h->z, n0);
         ALLOC(h, h->p, n0);
         ALLOC(h, h->q, n0);
+        for (auto& d : h->dring64) ALLOC(h, d, n0);
         h->fp64_ready = true;
     } else {
         ALLOC(h, h->r32, n0);
@@ -134,6 +135,7 @@ topo_status alloc_precision(topo_grid* h, bool fp64) {
         ALLOC(h, h->p32, n0);
         ALLOC(h, h->q32, n0);
         ALLOC(h, h->d32, n0);
+        for (auto& d : h->dring32) ALLOC(h, d, n0);
         h->fp32_ready = true;
     }
     return TOPO_OK;
@@ -165,7 +167,9 @@ void free_all(topo_grid* h) {
     F(h->cs.A); F(h->cs.W64); F(h->cs.WT64); F(h->cs.W32); F(h->cs.WT32); F(h->cs.y64); F(h->cs.y32);
     F(h->cs.info); F(h->cs.Dk);
     F(h->x); F(h->f); F(h->r); F(h->z); F(h->p); F(h->q);
-    F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32);
+    F(h->r32); F(h->z32); F(h->p32); F(h->q32); F(h->d32); F(h->alpha_hist);
+    for (auto& d : h->dring64) F(d);
+    for (auto& d : h->dring32) F(d);
     F(h->K0d); F(h->K0f);
     F(h->dc_work); F(h->xnew_work); F(h->oc_hi); F(h->G64); F(h->oc_dv); F(h->S_cache); F(h->dv_cache); F(h->offs); F(h->wts);
     F(h->lam); F(h->dtmp); F(h->dflag); F(h->tc_err); F(h->tcB); F(h->partials); F(h->sc);
@@ -178,7 +182,7 @@ void free_all(topo_grid* h) {
     h->mkdf = nullptr;
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->cap_stream = nullptr;
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kDirRing; ++q) {
         if (h->graph64[q].exec) cudaGraphExecDestroy(h->graph64[q].exec);
         if (h->graph32[q].exec) cudaGraphExecDestroy(h->graph32[q].exec);
         h->graph64[q].exec = h->graph32[q].exec = nullptr;
@@ -474,6 +478,7 @@ topo_status topo_create_grid(int nx, int ny, int nz, const topo_params* prm, voi
     TRY(dalloc(h, &h->tcB, kTcBWords));
     TRY(dalloc(h, &h->partials, (size_t)h->npartials));
     TRY(dalloc(h, &h->sc, 1));
+    TRY(dalloc(h, &h->alpha_hist, kDirRing));
     h->cs.n = (int)std::min<long long>(3 * h->lev[h->L - 1].g.nn, 1LL << 30);
     h->cs.npad = (h->cs.n + 31) / 32 * 32;
     TRY(alloc_precision(h, p.precision == TOPO_FP64));

@@ -84,6 +84,8 @@ struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
     double* Dk = nullptr;     // inverses of the 32 x 32 diagonal blocks of L (npad x 32)
 };
 
+constexpr int kDirRing = 8;   // CG direction buffers of the fused iterations
+
 struct PcgGraph {             // one captured PCG iteration (precond, beta, p, K p, alpha, x/r update)
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;   // kernel launches per replay
@@ -143,7 +145,13 @@ struct topo_grid {
     double* host_sc = nullptr;      // pinned host mirror
     bool have_density = false, have_bc = false, fp64_ready = false, fp32_ready = false, bf16_ready = false;
     long long launches = 0;
-    topo::PcgGraph graph64[2], graph32[2];   // captured PCG iterations per precision and direction buffer
+    // CG directions of the fused iterations: a ring of kDirRing buffers (p,
+    // level 0's v.b, and these), so that x += alpha p runs once per ring
+    // (cg_flush_x) instead of once per iteration
+    double* dring64[topo::kDirRing - 2] = {};
+    float* dring32[topo::kDirRing - 2] = {};
+    double* alpha_hist = nullptr;   // device: alpha of each ring slot
+    topo::PcgGraph graph64[topo::kDirRing], graph32[topo::kDirRing];   // captured PCG iterations per ring slot
     topo::PcgGraph coarse_graph;            // captured coarsest-grid assembly, factorization and inverse
     cudaStream_t cap_stream = nullptr;  // private stream the graphs are captured on
     topo_solve_stats stats{};
@@ -248,7 +256,8 @@ void dot_partials(const Ctx& c, long long n, const A* a, const B* b, double* par
 // reduces n partials into *dst (device double), fixed order
 void reduce_to(const Ctx& c, const double* partials, int n, double* dst);
 // CG scalar steps, all on device: alpha = rz/pq ; beta = rz_new/rz, rz = rz_new
-void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc);
+// hist != nullptr: alpha is also stored there (the direction ring's slot)
+void cg_alpha(const Ctx& c, const double* partials, int n, Scalars* sc, double* hist = nullptr);
 void cg_beta(const Ctx& c, const double* partials, int n, Scalars* sc);
 // flexible (Polak-Ribiere) beta for a preconditioner that varies between
 // applications: beta = z_new.(r_new - r_old) / z_old.r_old = -alpha z_new.q / rz_old,
@@ -259,6 +268,13 @@ void cg_update_xr(const Ctx& c, long long n, const Scalars* sc, const T* p, cons
                   double* partials);
 template <typename T>
 void cg_update_p(const Ctx& c, long long n, const Scalars* sc, const T* z, T* p);
+// r -= alpha q with partial sums of r.r (x updated later by cg_flush_x)
+template <typename T>
+void cg_update_r(const Ctx& c, long long n, const Scalars* sc, const T* q, T* r, double* partials);
+// x += alpha_j p_j for j = 0 .. count-1 in that order (the same operations as
+// count successive x += alpha p steps); p_j = ring[j], alpha_j = alpha[j]
+template <typename T>
+void cg_flush_x(const Ctx& c, long long n, T* const* ring, const double* alpha, int count, T* x);
 template <typename S, typename D>
 void convert(const Ctx& c, long long n, const S* src, D* dst);
 void axpy_f32_into_f64(const Ctx& c, long long n, const float* d, double* x);

@@ -33,6 +33,7 @@ struct P<double> {
     static double* y(topo_grid* h) { return h->cs.y64; }
     static const double* Ke(Level& l) { return l.Ke64; }
     static PcgGraph* graph(topo_grid* h) { return h->graph64; }
+    static double* const* dring(topo_grid* h) { return h->dring64; }
 };
 template <>
 struct P<float> {
@@ -46,6 +47,7 @@ struct P<float> {
     static float* y(topo_grid* h) { return h->cs.y32; }
     static const float* Ke(Level& l) { return l.Ke32; }
     static PcgGraph* graph(topo_grid* h) { return h->graph32; }
+    static float* const* dring(topo_grid* h) { return h->dring32; }
 };
 
 template <typename T>
@@ -320,24 +322,40 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
     // (ST_APPLY_P), which reads the old direction from one buffer and writes
     // the new one to the other; the tensor-core operator has no fused form.
     const bool fused = !(std::is_same<T, float>::value && h->prm.tensor_cores != 0);
-    T* pbuf[2] = {p, vb.b};   // vb.b of level 0 is free during the solve
+    // With the fused K.p, iteration k writes its direction to ring slot
+    // k % R and reads the previous one from the slot before; x += alpha p
+    // waits until the ring is full (or the solve ends) and is then applied
+    // for all its slots in one pass (cg_flush_x), in the order of the steps.
+    constexpr int R = kDirRing;
+    T* ring[R];
+    ring[0] = p;
+    ring[1] = vb.b;   // vb.b of level 0 is free during the solve
+    for (int j = 2; j < R; ++j) ring[j] = P<T>::dring(h)[j - 2];
     int np = precond();
     cg_beta(c, h->partials, np, h->sc);   // sets rz (beta unused on the first step)
     if (!fused) cudaMemcpyAsync(p, z, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream);
-    // K p, alpha, x += alpha p, r -= alpha q, r.r (on the stream current in h);
-    // first: p = z; else p = z + beta p_old from pold into pnew
-    auto step_a = [&](bool first, T* pold, T* pnew) {
+    // step k: K p, alpha, r -= alpha q, r.r, and x += alpha p (per step, or
+    // per full ring when fused) on the stream current in h; first step (k = 0):
+    // p = z, else p = z + beta p_old
+    auto step_a = [&](int k) {
         const Ctx cc = h->ctx();
-        // (the first step reads z in place of p_old: beta is absent, nothing is added)
-        const int npa = fused ? op_apply<T>(h, ST_APPLY_P, 0, z, first ? z : pold, q, h->partials, pnew,
-                                            first ? nullptr : &h->sc->beta)
-                              : op_apply<T>(h, ST_APPLY, 0, pnew, nullptr, q, h->partials);
-        cg_alpha(cc, h->partials, npa, h->sc);
-        cg_update_xr<T>(cc, n, h->sc, pnew, q, x, r, h->partials);
+        if (fused) {
+            const int s = k % R;
+            // (the first step reads z in place of p_old: beta is absent, nothing is added)
+            const int npa = op_apply<T>(h, ST_APPLY_P, 0, z, k == 0 ? z : ring[(s + R - 1) % R], q, h->partials,
+                                        ring[s], k == 0 ? nullptr : &h->sc->beta);
+            cg_alpha(cc, h->partials, npa, h->sc, h->alpha_hist + s);
+            cg_update_r<T>(cc, n, h->sc, q, r, h->partials);
+            if (s == R - 1) cg_flush_x<T>(cc, n, ring, h->alpha_hist, R, x);
+        } else {
+            const int npa = op_apply<T>(h, ST_APPLY, 0, p, nullptr, q, h->partials);
+            cg_alpha(cc, h->partials, npa, h->sc);
+            cg_update_xr<T>(cc, n, h->sc, p, q, x, r, h->partials);
+        }
         reduce_to(cc, h->partials, kRedBlocks, &h->sc->rr);
     };
-    // z = M^-1 r, beta, p = z + beta p (pbuf[par] -> pbuf[par ^ 1]), then K p ...
-    auto step_ba = [&](int par) {
+    // z = M^-1 r, beta, p = z + beta p, then K p ... (step k)
+    auto step_ba = [&](int k) {
         const Ctx cc = h->ctx();
         const int npb = precond();
         cg_beta(cc, h->partials, npb, h->sc);
@@ -345,22 +363,18 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
             dot_partials<T, T>(cc, n, z, q, h->partials);
             cg_beta_flexible(cc, h->partials, kRedBlocks, h->sc);
         }
-        if (fused) {
-            step_a(false, pbuf[par], pbuf[par ^ 1]);
-        } else {
-            cg_update_p<T>(cc, n, h->sc, z, p);
-            step_a(false, p, p);
-        }
+        if (!fused) cg_update_p<T>(cc, n, h->sc, z, p);
+        step_a(k);
     };
-    // Every iteration after the first is one of two fixed sequences of
-    // launches (the direction buffers alternate; all scalars live on the
-    // device), each captured once into a CUDA graph and replayed; the host
-    // only reads r.r between replays.  Not while launches are timed one by one.
+    // Every iteration after the first is one of R fixed sequences of
+    // launches (one per ring slot; all scalars live on the device), each
+    // captured once into a CUDA graph and replayed; the host only reads r.r
+    // between replays.  Not while launches are timed one by one.
     PcgGraph* grs = P<T>::graph(h);
-    const bool use_graph = h->prm.graphs != 0 && !h->prof_on && !grs[0].failed && !grs[1].failed;
-    step_a(true, nullptr, fused ? pbuf[0] : p);
-    int cur = 0;   // pbuf[cur] holds the current direction
-    int it = 1;
+    bool use_graph = h->prm.graphs != 0 && !h->prof_on;
+    for (int j = 0; j < R; ++j) use_graph = use_graph && !grs[j].failed;
+    step_a(0);
+    int it = 1;   // steps taken
     // The host reads r.r (one stream synchronisation) after a batch of
     // iterations: one at a time for the first two, then as many as the
     // observed contraction rate predicts are still needed (at most 8, and
@@ -391,20 +405,21 @@ static int pcg_core(topo_grid* h, T* x, T* r, T* z, T* p, T* q, double rr0, doub
         rr_prev = rr;
         last_batch = batch;
         for (int b = 0; b < batch; ++b) {
-            const int par = fused ? cur : 0;
-            PcgGraph& gr = grs[par];
-            if (use_graph && !gr.exec && it >= 2) capture_graph(h, gr, [&]() { step_ba(par); });
+            const int k = it;
+            PcgGraph& gr = grs[fused ? k % R : 0];
+            if (use_graph && !gr.exec && k >= 2) capture_graph(h, gr, [&]() { step_ba(k); });
             if (use_graph && gr.exec) {
                 cudaGraphLaunch(gr.exec, h->stream);
                 h->launches += gr.launches;
                 ++h->stats.graph_replays;
             } else {
-                step_ba(par);
+                step_ba(k);
             }
-            if (fused) cur ^= 1;
             ++it;
         }
     }
+    // the x updates of the steps since the last full ring (the last step is it - 1)
+    if (fused && (it - 1) % R != R - 1) cg_flush_x<T>(c, n, ring, h->alpha_hist, (it - 1) % R + 1, x);
     if (*status == TOPO_OK && rr > target_rr) *status = TOPO_MAXITER;
     *rr_out = rr;
     return it;
