@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(256) k_restrict_z(const uint8_t* __restrict__ 
     T lo[3], mid[3], hi[3];
     plane_sum(2 * K0 - 1, lo);
     const long long ccol = I + (long long)NXc * J, cplane = (long long)NXc * NYc;
+#pragma unroll 2
     for (int K = K0; K < K1; ++K) {
         plane_sum(2 * K, mid);
         plane_sum(2 * K + 1, hi);
@@ -110,7 +111,28 @@ __global__ void __launch_bounds__(256) k_prolong_z(const uint8_t* __restrict__ m
     T va[3], vb[3];
     int Ka = -1;   // coarse plane whose interpolation is held in va
     const long long col = i + (long long)NXf * j, fplane = (long long)NXf * NYf;
+    // the fine node's mask and iterate are loaded one plane ahead (before
+    // the stores of the current plane), so that each thread keeps a load in
+    // flight while it interpolates and stores
+    unsigned mf_n = 0u;
+    TU un[3];
+    if (k0 < k1) {
+        const long long n = col + fplane * k0;
+        mf_n = maskf[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) un[c] = uf[3 * n + c];
+    }
     for (int k = k0; k < k1; ++k) {
+        const unsigned mf = mf_n;
+        T uo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) uo[c] = (T)un[c];
+        if (k + 1 < k1) {
+            const long long n1 = col + fplane * (k + 1);
+            mf_n = maskf[n1];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) un[c] = uf[3 * n1 + c];
+        }
         const int K = k >> 1;
         if (Ka != K) {
             coarse_plane(K, va);
@@ -127,10 +149,9 @@ __global__ void __launch_bounds__(256) k_prolong_z(const uint8_t* __restrict__ m
             Ka = K + 1;
         }
         const long long n = col + fplane * k;
-        const unsigned mf = maskf[n];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (!((mf >> c) & 1u)) uf[3 * n + c] = (TU)((T)uf[3 * n + c] + val[c]);
+            if (!((mf >> c) & 1u)) uf[3 * n + c] = (TU)(uo[c] + val[c]);
     }
 }
 
