@@ -75,18 +75,44 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
+// Double-FP32 counterpart: the x and y components of a node as dfl2 (high
+// words in one float2, low words in another), so that each step of the
+// TwoSum-based add of dfloat.cuh runs as one paired instruction for both
+// components -- lane by lane the same IEEE operations as df_add / df_sub.
+struct dfl2 {
+    float2 h, l;
+};
+__device__ __forceinline__ dfl2 ld2(const dfl* p) {
+    return dfl2{make_float2(p[0].h, p[1].h), make_float2(p[0].l, p[1].l)};
+}
+__device__ __forceinline__ void st2(dfl* p, dfl2 v) {
+    p[0] = dfl{v.h.x, v.l.x};
+    p[1] = dfl{v.h.y, v.l.y};
+}
+__device__ __forceinline__ dfl2 add2(dfl2 a, dfl2 b) {
+    const float2 s = add2(a.h, b.h), t = add2(a.l, b.l);
+    const float2 v = sub2(s, a.h);
+    const float2 p = sub2(s, v), q = sub2(b.h, v);
+    const float2 e = add2(sub2(a.h, p), q);
+    return dfl2{s, add2(e, t)};
+}
+__device__ __forceinline__ dfl2 sub2(dfl2 a, dfl2 b) {
+    return add2(a, dfl2{make_float2(-b.h.x, -b.h.y), make_float2(-b.l.x, -b.l.y)});
+}
+
 template <typename T>
 __device__ __forceinline__ void face_forward(const T* c00, const T* c10, const T* c01, const T* c11, T* F) {
     // F[3*g + c], g = bx + 2 by
-    if constexpr (std::is_same<T, float>::value) {
-        const float2 s0 = add2(ld2(c10), ld2(c00)), d0 = sub2(ld2(c10), ld2(c00));
-        const float2 s1 = add2(ld2(c11), ld2(c01)), d1 = sub2(ld2(c11), ld2(c01));
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, dfl>::value) {
+        using V2 = std::conditional_t<std::is_same<T, float>::value, float2, dfl2>;
+        const V2 s0 = add2(ld2(c10), ld2(c00)), d0 = sub2(ld2(c10), ld2(c00));
+        const V2 s1 = add2(ld2(c11), ld2(c01)), d1 = sub2(ld2(c11), ld2(c01));
         st2(F + 0, add2(s1, s0));
         st2(F + 3, add2(d1, d0));
         st2(F + 6, sub2(s1, s0));
         st2(F + 9, sub2(d1, d0));
-        const float z0 = c10[2] + c00[2], e0 = c10[2] - c00[2];
-        const float z1 = c11[2] + c01[2], e1 = c11[2] - c01[2];
+        const T z0 = c10[2] + c00[2], e0 = c10[2] - c00[2];
+        const T z1 = c11[2] + c01[2], e1 = c11[2] - c01[2];
         F[2] = z1 + z0;
         F[5] = e1 + e0;
         F[8] = z1 - z0;
@@ -106,15 +132,16 @@ __device__ __forceinline__ void face_forward(const T* c00, const T* c10, const T
 
 template <typename T>
 __device__ __forceinline__ void face_inverse(const T* A, T* c00, T* c10, T* c01, T* c11) {
-    if constexpr (std::is_same<T, float>::value) {
-        const float2 lo0 = sub2(ld2(A + 0), ld2(A + 6)), hi0 = add2(ld2(A + 0), ld2(A + 6));
-        const float2 lo1 = sub2(ld2(A + 3), ld2(A + 9)), hi1 = add2(ld2(A + 3), ld2(A + 9));
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, dfl>::value) {
+        using V2 = std::conditional_t<std::is_same<T, float>::value, float2, dfl2>;
+        const V2 lo0 = sub2(ld2(A + 0), ld2(A + 6)), hi0 = add2(ld2(A + 0), ld2(A + 6));
+        const V2 lo1 = sub2(ld2(A + 3), ld2(A + 9)), hi1 = add2(ld2(A + 3), ld2(A + 9));
         st2(c00, sub2(lo0, lo1));
         st2(c10, add2(lo0, lo1));
         st2(c01, sub2(hi0, hi1));
         st2(c11, add2(hi0, hi1));
-        const float l0 = A[2] - A[8], h0 = A[2] + A[8];
-        const float l1 = A[5] - A[11], h1 = A[5] + A[11];
+        const T l0 = A[2] - A[8], h0 = A[2] + A[8];
+        const T l1 = A[5] - A[11], h1 = A[5] + A[11];
         c00[2] = l0 - l1;
         c10[2] = l0 + l1;
         c01[2] = h0 - h1;
@@ -140,7 +167,7 @@ template <typename T>
 __device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* FB, const T* FT, T* Bo, T* To,
                                               const T* zc = nullptr) {
     T m[24];
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, dfl>::value) {
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             st2(m + 3 * g, add2(ld2(FT + 3 * g), ld2(FB + 3 * g)));
@@ -198,7 +225,7 @@ __device__ __forceinline__ void element_modal(const ModalK<T>& k, T E, const T* 
         Bo[c] = -w[12 + c];
         To[c] = w[12 + c];
     }
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, dfl>::value) {
 #pragma unroll
         for (int g = 1; g < 4; ++g) {
             st2(Bo + 3 * g, sub2(ld2(w + 3 * g), ld2(w + 3 * (g + 4))));

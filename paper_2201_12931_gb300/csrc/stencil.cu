@@ -275,8 +275,13 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                 ld3(Cb + coff - 4, a0);
                 ld3(Cb + nC / 3 + coff - TX * 4, a1);
                 ld3(Cb + 2 * (nC / 3) + coff - TX * 4 - 4, a2);
+                if constexpr (kDF) {   // x and y in paired form (the same operations)
+                    st2(y, add2(add2(add2(ld2(st00), ld2(a0)), ld2(a1)), ld2(a2)));
+                    y[2] = st00[2] + a0[2] + a1[2] + a2[2];
+                } else {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
+                    for (int c = 0; c < 3; ++c) y[c] = st00[c] + a0[c] + a1[c] + a2[c];
+                }
             }
             // D^-1 of the output node: stored (first two sweeps) or formed
             // from the column sums of E over the two layers around plane Q
@@ -343,10 +348,20 @@ __global__ void __launch_bounds__(kOpTX * op_ty<T>(), sizeof(T) == 4 ? 2 : 1)
                     element_modal<T>(mk, sE[B], fb[B2 ^ 1], fb[B2], Bo, To);
                 }
                 T A[12];
+                if constexpr (kDF) {   // x and y of each corner group in paired form
 #pragma unroll
-                for (int i = 0; i < 12; ++i) {
-                    A[i] = top[i] + Bo[i];
-                    top[i] = To[i];
+                    for (int g = 0; g < 4; ++g) {
+                        st2(A + 3 * g, add2(ld2(top + 3 * g), ld2(Bo + 3 * g)));
+                        A[3 * g + 2] = top[3 * g + 2] + Bo[3 * g + 2];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) top[i] = To[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 12; ++i) {
+                        A[i] = top[i] + Bo[i];
+                        top[i] = To[i];
+                    }
                 }
                 face_inverse<T>(A, st00, st10, st01, st11);
                 if constexpr (kDF) {
