@@ -117,7 +117,7 @@ topo_status topo_default_params(topo_params* p);
  * 2^(levels-1), bad parameter, or 3 * (nx+1)(ny+1)(nz+1) >= 2^31 (the
  * operator kernels index nodal vectors with 32-bit integers: up to about
  * 715M nodes, e.g. 1152x768x768 elements, a mixed-precision handle of
- * roughly 150 GB).  Calls that need the coarsest-grid solve
+ * roughly 220 GB).  Calls that need the coarsest-grid solve
  * (topo_solve_state, topo_vcycle) return TOPO_BADARG if that grid has more
  * than 12000 DOFs.
  * TOPO_OOM / TOPO_CUDA: allocation or device failure (no handle returned).
