@@ -86,7 +86,7 @@ struct Coarse {           // dense coarsest-grid solve: K_c^-1 = W^T W, W = L^-1
 
 constexpr int kDirRing = 8;   // CG direction buffers of the fused iterations
 
-struct PcgGraph {             // one captured PCG iteration (precond, beta, p, K p, alpha, x/r update)
+struct PcgGraph {             // a captured launch sequence (a PCG iteration, or the coarsest factorization)
     cudaGraphExec_t exec = nullptr;
     long long launches = 0;   // kernel launches per replay
     bool failed = false;      // capture not possible: direct launches

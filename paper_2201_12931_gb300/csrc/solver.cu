@@ -4,9 +4,11 @@
 //     restriction, recursion from a zero iterate, prolongation correction and
 //     the direct solve on the coarsest grid;
 //   * preconditioned CG (Algorithm 1, standard initialisation r0 = f - K x0,
-//     z0 = M^-1 r0, p0 = z0), scalars kept on the device; iterations after
-//     the first replayed from a captured CUDA graph; flexible beta for the
-//     BF16-iterate V-cycle;
+//     z0 = M^-1 r0, p0 = z0), scalars kept on the device; the direction
+//     update fused into K.p, directions kept in a ring of 8 buffers with
+//     x += alpha p applied once per ring; iterations after the first
+//     replayed from captured CUDA graphs (one per ring slot); flexible beta
+//     for the BF16-iterate V-cycle;
 //   * FP64 iterative refinement around an FP32 inner MGPCG (mixed modes):
 //     r = f - K x in FP64, solve K d ~= r in FP32, x += d, repeat.
 #include <chrono>
