@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(128) k_potrf_diag(double* __restrict__ A, int 
         __syncthreads();
         if (tid > j && tid < TB) sA[tid][j] *= sR[j];
         __syncthreads();
-        for (int e = tid; e < TB * TB; e += 128) {
+        for (int e = (j + 1) * TB + tid; e < TB * TB; e += 128) {   // rows below j only
             const int i = e / TB, k = e % TB;
             if (k > j && k <= i) sA[i][k] -= sA[i][j] * sA[k][j];
         }
@@ -304,9 +304,9 @@ __global__ void __launch_bounds__(128) k_potrf_diag(double* __restrict__ A, int 
     for (int j = 0; j < TB; ++j) {
         if (tid <= j) sX[j][tid] *= sR[j];
         __syncthreads();
-        for (int e = tid; e < TB * TB; e += 128) {
+        for (int e = (j + 1) * TB + tid; e < TB * TB; e += 128) {   // rows below j only
             const int i = e / TB, c = e % TB;
-            if (i > j && c <= j) sX[i][c] -= sA[i][j] * sX[j][c];
+            if (c <= j) sX[i][c] -= sA[i][j] * sX[j][c];
         }
         __syncthreads();
     }
