@@ -157,3 +157,40 @@ def test_graph_replay_is_bitwise_identical(precision):
     assert r1.graph_replays > 0 and r0.graph_replays == 0
     assert r1.iters == r0.iters
     assert np.array_equal(u1, u0)
+
+
+def test_direction_ring_wraps_and_flushes():
+    """The CG directions live in a ring of 8 buffers and x += alpha p is
+    applied once per full ring (inside the captured iteration of slot 7) and
+    for the remainder when the run stops.  A single FP64 CG run of more than
+    two ring lengths, with graphs and with direct launches, reaches the
+    oracle's solution and both runs agree bitwise; a run stopped after 11
+    steps (one full ring and 3 more) returns an x whose FP64 residual,
+    recomputed from the oracle's assembled K, is the one it reports."""
+    from paper_2201_12931_gb300 import Params, TopoGrid, TOPO_MAXITER
+    from oracle import assemble, element
+    import torch
+    dims, levels = (32, 16, 16), 2     # two levels: slow enough for > 16 iterations
+    rho = synth.uniform_field(dims, 7, 1e-3, 1.0)
+    pb = synth.cantilever(dims)
+    u_o = ostate.solve_state(dims, rho, pb.fixed, pb.f, tol=1e-13)
+    K = assemble.apply_dirichlet(assemble.assemble(dims, assemble.simp_modulus(rho, 1.0, 1e-9, 3.0),
+                                                   element.element_stiffness(0.3)), pb.fixed)
+    out = []
+    for graphs in (1, 0):
+        g = TopoGrid(dims, Params(levels=levels, precision=0, graphs=graphs))
+        g.set_density(t(rho))
+        g.set_bc_loads(t(pb.fixed), t(pb.f))
+        u = torch.empty(3 * g.nn, dtype=torch.float64, device=cuda_device())
+        _, res = g.solve(1e-11, 2000, out=u)
+        assert res.status == 0 and res.iters > 16, res
+        out.append(n(u))
+        g.reset_solution()
+        u2 = torch.empty_like(u)
+        _, r2 = g.solve(1e-14, 11, out=u2)
+        assert r2.status == TOPO_MAXITER and r2.iters == 11
+        rr = np.linalg.norm(pb.f - K @ n(u2)) / np.linalg.norm(pb.f)
+        assert abs(rr - r2.relres) <= 1e-6 * rr
+        g.close()
+    assert np.array_equal(out[0], out[1])
+    assert np.linalg.norm(out[0] - u_o) <= 1e-8 * np.linalg.norm(u_o)
