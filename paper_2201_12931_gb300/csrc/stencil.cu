@@ -503,12 +503,8 @@ __device__ __forceinline__ double ipow(double r, double p, int ip) {
 }
 
 // Element energy u_e^T K0 u_e in the modal (Walsh-Hadamard) basis, compliance
-// partial sums sum_e E_e se_e and the sensitivity -p rho^(p-1) (E0-Emin) se_e.
-// LOW = true (mixed-precision handles): the corner-0 displacement is
-// subtracted in FP64 (K0 annihilates translations, so the energy is
-// unchanged), and the small relative displacements are transformed and
-// contracted in FP32; the compliance is still accumulated in FP64.
-template <bool LOW>
+// partial sums sum_e E_e se_e and the sensitivity -p rho^(p-1) (E0-Emin) se_e,
+// in FP64 (FP64 handles; mixed-precision handles use k_energy_sens_z).
 __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double* __restrict__ u,
                                                      const double* __restrict__ rho, int nx, int ny, int nz,
                                                      double E0, double Emin, double penal, int ipenal,
@@ -522,39 +518,88 @@ __global__ void __launch_bounds__(256) k_energy_sens(ModalCoef mc, const double*
         const int i = (int)(e % nx);
         const long long t = e / nx;
         const int j = (int)(t % ny), k = (int)(t / ny);
-        double se;
-        if (LOW) {
-            const long long n0 = i + (long long)NX * (j + (long long)NY * k);
-            const double r0 = u[3 * n0], r1 = u[3 * n0 + 1], r2 = u[3 * n0 + 2];
-            float ue[24];
-            ue[0] = ue[1] = ue[2] = 0.f;
+        double ue[24];
 #pragma unroll
-            for (int a = 1; a < 8; ++a) {
-                const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
-                ue[3 * a + 0] = (float)(u[3 * nd + 0] - r0);
-                ue[3 * a + 1] = (float)(u[3 * nd + 1] - r1);
-                ue[3 * a + 2] = (float)(u[3 * nd + 2] - r2);
-            }
-            float m[24];
-            modal_forward(ue, m);
-            se = (double)modal_energy<float>(mc, m);
-        } else {
-            double ue[24];
+        for (int a = 0; a < 8; ++a) {
+            const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                const long long nd = (i + (a & 1)) + (long long)NX * ((j + ((a >> 1) & 1)) + (long long)NY * (k + (a >> 2)));
-#pragma unroll
-                for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nd + c];
-            }
-            double m[24];
-            modal_forward(ue, m);
-            se = modal_energy(mc, m);
+            for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nd + c];
         }
+        double m[24];
+        modal_forward(ue, m);
+        const double se = modal_energy(mc, m);
         const double r = rho[e];
         const double rp1 = ipenal >= 1 ? ipow(r, penal - 1.0, ipenal - 1) : pow(r, penal - 1.0);
         const double Ee = Emin + rp1 * r * (E0 - Emin);
         csum += Ee * se;
         if (dc) dc[e] = -penal * rp1 * (E0 - Emin) * se;
+    }
+    const double tsum = block_sum(csum, sred);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tsum;
+}
+
+// Mixed-precision handles: the corner-0 displacement is subtracted (K0
+// annihilates translations, so the energy is unchanged) and the small
+// relative displacements are transformed and contracted in FP32; the
+// compliance is still accumulated in FP64.  The subtraction uses the integer
+// split of each FP64 value into FP32 words h + l (dfloat.cuh): (h - h0) +
+// (l - l0) in FP32 carries the difference to FP32 accuracy without FP64
+// instructions, which run on a narrow pipe.  Indices are 32-bit (the grid
+// limit of create_grid).
+// Marching along z: a work item is an (i, j) element column and a chunk of
+// cz layers; the upper face
+// of one element (4 nodes, split once into FP32 words) is the lower face of
+// the next, so every node is read and split about once per chunk instead of
+// once per element around it; the FP64 compliance partials are summed per
+// thread in z order.
+__global__ void __launch_bounds__(256) k_energy_sens_z(ModalCoef mc, const double* __restrict__ u,
+                                                       const double* __restrict__ rho, int nx, int ny, int nz,
+                                                       int cz, double E0, double Emin, double penal, int ipenal,
+                                                       double* __restrict__ dc, double* __restrict__ partials) {
+    __shared__ double sred[32];
+    const int NX = nx + 1, NY = ny + 1;
+    const int ncol = nx * ny, nplane = NX * NY, nchunk = (nz + cz - 1) / cz;
+    const int items = ncol * nchunk;
+    double csum = 0.0;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const int col = it % ncol, q = it / ncol;
+        const int i = col % nx, j = col / nx;
+        const int k0 = q * cz, k1 = min(nz, k0 + cz);
+        const int n00 = i + NX * j;
+        dfl lo[12], hi[12];
+        auto face = [&](int k, dfl* f) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int nd = n00 + (a & 1) + NX * (a >> 1) + nplane * k;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f[3 * a + c] = df_from_double(u[3 * nd + c]);
+            }
+        };
+        face(k0, lo);
+        for (int k = k0; k < k1; ++k) {
+            face(k + 1, hi);
+            float ue[24];
+            ue[0] = ue[1] = ue[2] = 0.f;
+#pragma unroll
+            for (int a = 1; a < 8; ++a) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const dfl v = a < 4 ? lo[3 * a + c] : hi[3 * (a - 4) + c];
+                    ue[3 * a + c] = __fadd_rn(__fsub_rn(v.h, lo[c].h), __fsub_rn(v.l, lo[c].l));
+                }
+            }
+            float m[24];
+            modal_forward(ue, m);
+            const double se = (double)modal_energy<float>(mc, m);
+            const int e = col + ncol * k;
+            const double r = rho[e];
+            const double rp1 = ipenal >= 1 ? ipow(r, penal - 1.0, ipenal - 1) : pow(r, penal - 1.0);
+            const double Ee = Emin + rp1 * r * (E0 - Emin);
+            csum += Ee * se;
+            if (dc) dc[e] = -penal * rp1 * (E0 - Emin) * se;
+#pragma unroll
+            for (int x = 0; x < 12; ++x) lo[x] = hi[x];
+        }
     }
     const double tsum = block_sum(csum, sred);
     if (threadIdx.x == 0) partials[blockIdx.x] = tsum;
@@ -674,11 +719,18 @@ void assemble_coarse(const Ctx& c, const Geom& g, const double* K0, const double
 void element_energy_sens(const Ctx& c, const Geom& g, const ModalCoef& mc, const double* u, const double* rho,
                          double E0, double Emin, double penal, double* dc_out, double* partials, bool low) {
     const int ip = (penal == (double)(int)penal && penal >= 1.0 && penal <= 16.0) ? (int)penal : -1;
-    if (low)
-        k_energy_sens<true><<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, ip, dc_out,
-                                                           partials);
-    else
-        k_energy_sens<false><<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, ip, dc_out,
+    if (low) {
+        // chunks of the z columns so that every thread of the fixed grid gets
+        // about four work items (a chunk re-reads one face)
+        const long long ncol = (long long)g.nx * g.ny, threads = (long long)kRedBlocks * 256;
+        long long nch = (4 * threads + ncol - 1) / ncol;
+        if (nch > g.nz) nch = g.nz;
+        if (nch < 1) nch = 1;
+        const int cz = (int)((g.nz + nch - 1) / nch);
+        k_energy_sens_z<<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, cz, E0, Emin, penal, ip, dc_out,
+                                                      partials);
+    } else
+        k_energy_sens<<<kRedBlocks, 256, 0, c.s>>>(mc, u, rho, g.nx, g.ny, g.nz, E0, Emin, penal, ip, dc_out,
                                                             partials);
     TOPO_LAUNCH_CHECK(c);
 }
