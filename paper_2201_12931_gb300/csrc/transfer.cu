@@ -57,7 +57,6 @@ __global__ void __launch_bounds__(256) k_restrict_z(const uint8_t* __restrict__ 
     T lo[3], mid[3], hi[3];
     plane_sum(2 * K0 - 1, lo);
     const long long ccol = I + (long long)NXc * J, cplane = (long long)NXc * NYc;
-#pragma unroll 2
     for (int K = K0; K < K1; ++K) {
         plane_sum(2 * K, mid);
         plane_sum(2 * K + 1, hi);
